@@ -1,0 +1,149 @@
+/*
+ * lsp.h -- C ABI of the GB300 (sm_103a) Lomb-Scargle periodogram engine.
+ *
+ * The engine evaluates the normalized Lomb-Scargle periodogram of an
+ * unevenly sampled series (Townsend, "Fast Calculation of the Lomb-Scargle
+ * Periodogram Using Graphics Processing Units", Sec. 3, Eq. 1-2, computed
+ * through the single-pass sums of Eq. 5-8) on a uniform frequency grid
+ * (Sec. 4.2, Eq. 9-11).  All arithmetic runs in the library's own CUDA
+ * kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers may be device pointers (cudaMalloc / torch CUDA tensors) or host
+ *   pointers (pageable or pinned).  The kind is detected per pointer.  Host
+ *   inputs are copied to library-owned device buffers; a host output makes
+ *   the call block until the result has been copied back.  With device
+ *   pointers only, a call is asynchronous on the context's stream: it returns
+ *   after argument checks and kernel launches, and errors found on the device
+ *   (non-finite data, zero variance) are reported by lsp_sync().
+ * - The caller owns every array it passes; the library owns only the context
+ *   and its workspace (grown on demand, freed by lsp_destroy).
+ * - Every function returns an lsp_status; lsp_last_error() gives the text of
+ *   the last failure on that context.  A failed call leaves outputs undefined.
+ * - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LSP_H
+#define LSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LSP_ABI_VERSION 1
+
+typedef struct lsp_ctx lsp_ctx;
+
+typedef enum lsp_status {
+    LSP_OK = 0,
+    LSP_ERR_INVALID_ARG = 1,  /* size, grid or pointer argument out of range   */
+    LSP_ERR_DEGENERATE = 2,   /* the data have zero variance (Sec. 3 needs >0)  */
+    LSP_ERR_NONFINITE = 3,    /* NaN or Inf among t, X or the grid               */
+    LSP_ERR_OOM = 4,          /* workspace allocation failed                     */
+    LSP_ERR_CUDA = 5,         /* a CUDA runtime call failed (text in last_error) */
+    LSP_ERR_TIMEOUT = 6,      /* lsp_sync deadline passed; work still queued     */
+    LSP_ERR_NO_MODEL = 7,     /* false-alarm surrogate has no weights loaded     */
+    LSP_ERR_UNSUPPORTED = 8   /* option combination not provided                 */
+} lsp_status;
+
+/* How sin/cos of the phase are produced in the O(N_t N_f) loop. */
+typedef enum lsp_sincos_mode {
+    LSP_SINCOS_AUTO = 0,   /* the library's choice (currently RECUR)                     */
+    LSP_SINCOS_MUFU = 1,   /* hardware sin/cos (SFU) of every phase (Sec. 4.3's choice)  */
+    LSP_SINCOS_RECUR = 2   /* SFU seed per strip of adjacent frequencies, then the
+                              angle-addition rotation by (cos, sin)(2 pi t_j df) on FMA */
+} lsp_sincos_mode;
+
+/* How the phase f_k t_j is formed. */
+typedef enum lsp_phase_mode {
+    LSP_PHASE_FIXED64 = 0,    /* exact: frac(t_j df), frac(t_j f_0) as 64-bit fixed-point
+                                 turns, phase = v_j + k u_j mod 2^64                      */
+    LSP_PHASE_NAIVE_FP32 = 1  /* the paper's single-precision f*t minus rintf (Sec. 4.3);
+                                 a comparator that loses accuracy when f*t is large     */
+} lsp_phase_mode;
+
+typedef struct lsp_options {
+    int32_t sincos_mode;      /* lsp_sincos_mode                                       */
+    int32_t phase_mode;       /* lsp_phase_mode                                        */
+    int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|16 */
+    int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
+    int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
+    int32_t reserved[7];      /* must be zero                                          */
+} lsp_options;
+
+/* Fill *opt with the defaults (AUTO sin/cos, FIXED64 phase, automatic launch shape). */
+void lsp_default_options(lsp_options *opt);
+
+/*
+ * Create a context on CUDA device `device`.  `opt` may be NULL (defaults).
+ * `cuda_stream` is a cudaStream_t to run on, or NULL for a stream the
+ * context creates and owns.  *out receives the context.
+ * Errors: INVALID_ARG (bad device or options), CUDA.
+ */
+lsp_status lsp_create(lsp_ctx **out, int device, const lsp_options *opt, void *cuda_stream);
+
+/* Replace the context's options (same rules as lsp_create). */
+lsp_status lsp_set_options(lsp_ctx *ctx, const lsp_options *opt);
+
+/* Make later calls run on `cuda_stream` (NULL: the context's own stream). */
+lsp_status lsp_set_stream(lsp_ctx *ctx, void *cuda_stream);
+
+/*
+ * Normalized Lomb-Scargle periodogram on a uniform grid (Eq. 1-2 through
+ * Eq. 5-8; the grid of Eq. 9 with an explicit origin):
+ *     P_out[k] = P_n(f_0 + k df),  k = 0 .. N_f-1.
+ * t[N_t]: sample times (FP64, any order, any origin; a common offset does
+ * not change P_n).  X[N_t]: measurements (FP64); the library shifts and
+ * scales them to zero mean and unit population variance (Sec. 3).  f_0, df:
+ * grid origin and spacing in cycles per time unit (any finite values; the
+ * paper's grid is f_0 = df, see lsp_grid).  P_out[N_f]: FP32 output.
+ * N_t >= 2, 0 <= N_f < 2^31.  N_f = 0 is a no-op.  A term of Eq. 1 whose
+ * denominator falls below N_t * 2^-16 (e.g. the sine term at the Nyquist
+ * frequency of an even grid) is taken as zero.
+ * Errors: INVALID_ARG, NONFINITE (f_0/df at call time; t/X on the device),
+ * DEGENERATE (zero variance, on the device), OOM, CUDA.
+ */
+lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64_t N_t,
+                           double f_0, double df, int64_t N_f, float *P_out);
+
+/*
+ * Grid helper, Eq. 10-11 with Eq. 9's origin: df = 1/(F_over (t_max - t_min)),
+ * N_f = floor(F_high F_over N_t / 2), f_0 = df.  Host-only arithmetic.
+ * Errors: INVALID_ARG (t_max <= t_min, F_over <= 0, F_high <= 0, N_t < 1).
+ */
+lsp_status lsp_grid(double t_min, double t_max, int64_t N_t, double F_over, double F_high,
+                    double *f_0, double *df, int64_t *N_f);
+
+/*
+ * Wait for the context's queued work, at most `timeout_s` seconds (< 0: no
+ * limit), polling a CUDA event.  Returns TIMEOUT if the deadline passes (the
+ * work stays queued), else the first device-detected data error of the calls
+ * since the previous lsp_sync (DEGENERATE / NONFINITE), else OK.
+ */
+lsp_status lsp_sync(lsp_ctx *ctx, double timeout_s);
+
+/*
+ * CUDA-event durations (milliseconds) of the kernels of the last call, when
+ * the context's `timing` option is set: prep (normalization + phase
+ * records), main (the O(N_t N_f) evaluation) and finalize (split reduction
+ * and Eq. 5).  Blocks until those events complete.  Any pointer may be NULL.
+ * Errors: INVALID_ARG (timing off or no call yet), CUDA.
+ */
+lsp_status lsp_last_timing(lsp_ctx *ctx, float *ms_prep, float *ms_main, float *ms_finalize);
+
+/* Kernel launches made by the last call (0 before the first). */
+int32_t lsp_last_launch_count(const lsp_ctx *ctx);
+
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+const char *lsp_last_error(const lsp_ctx *ctx);
+
+/* Release the context, its stream (if owned) and its workspace.  NULL is a no-op. */
+void lsp_destroy(lsp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSP_H */
