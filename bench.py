@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Benchmark: normalized Lomb-Scargle periodogram throughput on GB300.
+
+Workload (one step = one lsp_periodogram call = prep + main + finalize):
+``gapped_100k`` -- 100,000 samples over 1000 d with nightly gaps, three
+sinusoids + noise, oversampling 4, 200,000 frequencies (2e10 terms).  Inputs
+are resident in HBM when the timed region starts; the L2 is flushed between
+timed steps (inputs are 2.4 MB, smaller than L2).  Metric: L-S terms/s
+(N_t * N_f per second), whole job.
+
+With --gpus N (launched by torchrun) every rank evaluates its own block of
+200,000 frequencies of one longer grid (rank r starts at f_0 + r N_f df): the
+frequencies are independent, so there is no data-path collective and the
+scaling is weak.
+
+``--impl reference`` times the FP64 CPU oracle (the only other implementation
+this project has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import shutil
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "L-S terms/s (N_t·N_f) & % SFU/FMA peak; batched MC curves/s vs plain"
+UNIT = "terms/s"
+WORKLOAD = "gapped_100k"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("ls_main.cu", "lsp_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_1007_1658_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "ls_main_gapped_100k.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"traffic_record:\s*(\{.*?\})", txt)
+    if not m:
+        return None
+    rec = json.loads(m.group(1))
+    if rec.get("kernel_sha") != _kernel_sha() or rec.get("kernel") != kernel:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            self.proc = subprocess.Popen([exe, "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_sample(c, n_bins: int):
+    """Oracle (as it stands) on the first n_bins frequencies of the workload."""
+    import oracle
+    fr = c.f0 + np.arange(n_bins) * c.df
+    t0 = time.perf_counter()
+    oracle.periodogram_at(c.t, c.X, fr)
+    dt = time.perf_counter() - t0
+    terms = c.t.size * n_bins
+    return {"value": terms / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%s: all %d samples x first %d of %d frequencies (%.3g terms), FP64 two-pass Eq. 1-2"
+                      % (WORKLOAD, c.t.size, n_bins, c.nf, terms),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    from paper_1007_1658_gb300 import synth
+    if rank != 0:
+        return 0
+    c = synth.gapped_100k()
+    n_bins = args.ref_bins
+    for _ in range(args.warmup):
+        cpu_baseline_sample(c, max(8, n_bins // 16))
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline_sample(c, n_bins)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    terms = c.t.size * n_bins * args.steps
+    value = terms / sum(secs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N_t": int(c.t.size), "N_f": int(c.nf),
+                                            "sample_bins": n_bins},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_1007_1658_gb300 import lsp, synth
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = synth.gapped_100k()
+    f0 = c.f0 + rank * c.nf * c.df  # this rank's block of the grid
+    terms = c.t.size * c.nf
+    t_d = torch.from_numpy(c.t).to(dev)
+    X_d = torch.from_numpy(c.X).to(dev)
+    P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.Stream(device=dev)
+    ctx = lsp.Context(local, stream=stream, timing=1, sincos_mode=args.mode)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ctx.periodogram(t_d, X_d, f0, c.df, c.nf, out=P_d)
+        ctx.sync(120.0)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    main_ms, launches = [], 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+                ev[i][0].record(stream)
+                ctx.periodogram(t_d, X_d, f0, c.df, c.nf, out=P_d)
+                ev[i][1].record(stream)
+            _, m, fin = ctx.last_timing()
+            main_ms.append(m)
+            launches += ctx.last_launch_count()
+        ctx.sync(120.0)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * terms * args.steps / (total_ms * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    t_h = torch.from_numpy(c.t).pin_memory()
+    X_h = torch.from_numpy(c.X).pin_memory()
+    P_h = torch.empty(c.nf, dtype=torch.float32).pin_memory()
+    ctx_h = lsp.Context(local, stream=stream, sincos_mode=args.mode)
+    ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)
+    e2e_s = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)  # blocks until P_h is written
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_val = world * terms * len(e2e_s) / sum(e2e_s)
+    ctx_h.close()
+
+    if rank != 0:
+        ctx.close()
+        return 0
+    peaks, peak_src = _peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mode = args.mode if args.mode else lsp.SINCOS_RECUR
+    terms_per_clk = 16.0 if mode == lsp.SINCOS_RECUR else 8.0
+    peak = terms_per_clk * sms * peaks["sm_max_mhz"] * 1e6
+    achieved = terms / (float(np.mean(main_ms)) * 1e-3)
+    kernel = "ls_main_kernel<16,2>" if mode == lsp.SINCOS_RECUR else "ls_main_kernel<8,1>"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N_t": int(c.t.size), "N_f": int(c.nf), "terms_per_step": terms,
+                   "sincos": "recurrence" if mode == lsp.SINCOS_RECUR else "mufu", "phase": "fixed64",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "frequency shards x%d" % world},
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e9, "peak": peak / 1e9,
+                     "unit": "Gterms/s", "frac": achieved / peak, "traffic": _recorded_traffic(kernel),
+                     "peak_basis": "%s: %d terms/clk/SM x %d SMs x %.0f MHz (%s sm_max_mhz)" % (
+                         "FMA pipe, 8 FP32 ops/term" if mode == lsp.SINCOS_RECUR else "SFU, 2 MUFU ops/term",
+                         terms_per_clk, sms, peaks["sm_max_mhz"], peak_src),
+                     "main_ms": float(np.mean(main_ms))},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c.t.nbytes + c.X.nbytes),
+                "d2h_bytes_per_step": int(c.nf * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(c, args.cpu_bins).items() if k != "seconds"}
+    if args.batch:
+        line["batched_mc"] = run_batch_bench(ctx, torch, dev, stream, args)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_batch_bench(ctx, torch, dev, stream, args):
+    """Config-4 Monte-Carlo batch: one graph-captured persistent launch vs one
+    lsp_periodogram launch per curve (filled in once lsp_batch exists)."""
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--mode", type=int, default=0, help="sin/cos mode: 0 auto, 1 MUFU, 2 recurrence")
+    ap.add_argument("--ref-bins", type=int, default=2048, help="reference arm: oracle frequencies per step")
+    ap.add_argument("--cpu-bins", type=int, default=16384, help="cpu_baseline: oracle frequencies (~10-30 s)")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as d
+        backend = "nccl" if (args.impl == "gb300" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        d.init_process_group(backend=backend)
+        dist = d
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_gpu(args, rank, world, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

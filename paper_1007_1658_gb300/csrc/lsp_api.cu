@@ -1,0 +1,376 @@
+// lsp_api.cu -- the C ABI of include/lsp.h: context, workspace, argument
+// checks, launch-shape choice and the host<->device staging of host pointers.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+
+#include "lsp.h"
+#include "lsp_kernels.cuh"
+
+using lsp::CurveStats;
+using lsp::MainShape;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct lsp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    lsp_options opt{};
+    std::string err;
+    int sms = 0;
+    // workspace
+    DevBuf recA, recB, recN, part, stats, t_stage, x_stage, p_stage;
+    int* status_d = nullptr;  // device status word (OR of kStatus* bits)
+    int* status_h = nullptr;  // pinned mirror
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t done = nullptr;
+    bool timing_valid = false;
+    bool has_finalize = false;
+    int last_launches = 0;
+};
+
+namespace {
+
+// Makes the context's device current for the scope of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+lsp_status fail(lsp_ctx* ctx, lsp_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+lsp_status cuda_fail(lsp_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LSP_ERR_OOM : LSP_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LSP_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Grow a workspace buffer to at least `bytes` (contents are not kept).
+lsp_status ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap) return LSP_OK;
+    if (b.p) {
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        LSP_CUDA(ctx, cudaFree(b.p));
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+    }
+    b.cap = want;
+    return LSP_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
+    if (o->sincos_mode < 0 || o->sincos_mode > 2)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "sincos_mode %d out of range", o->sincos_mode);
+    if (o->phase_mode < 0 || o->phase_mode > 1)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "phase_mode %d out of range", o->phase_mode);
+    if (o->freqs_per_thread != 0 && o->freqs_per_thread != 4 && o->freqs_per_thread != 8 &&
+        o->freqs_per_thread != 16)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8 or 16");
+    if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");
+    for (int i = 0; i < 7; ++i)
+        if (o->reserved[i] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "reserved option fields must be zero");
+    return LSP_OK;
+}
+
+// Launch shape: mode, strip length F, N_t split.  The split is chosen so the
+// grid fills whole waves of resident CTAs while every chunk keeps at least
+// one tile of samples.
+MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
+    MainShape s{};
+    const lsp_options& o = ctx->opt;
+    if (o.phase_mode == LSP_PHASE_NAIVE_FP32)
+        s.mode = 3;
+    else
+        s.mode = o.sincos_mode == LSP_SINCOS_MUFU ? 1 : 2;
+    s.F = o.freqs_per_thread ? o.freqs_per_thread : (s.mode == 2 ? 16 : 8);
+    const int64_t per_block = lsp::freqs_per_block(s.F);
+    s.nfb = (int)((N_f + per_block - 1) / per_block);
+    s.nf_pad = (int64_t)s.nfb * per_block;
+    int split = o.split;
+    if (split <= 0) {
+        const int occ = std::max(1, lsp::main_occupancy(s.mode, s.F));
+        const int64_t slots = (int64_t)occ * std::max(1, ctx->sms);
+        const int64_t max_split = std::max<int64_t>(1, N / lsp::kTile);
+        double best = -1.0;
+        int best_s = 1;
+        for (int64_t sp = 1; sp <= std::min<int64_t>(max_split, 256); ++sp) {
+            const int64_t ctas = (int64_t)s.nfb * sp;
+            const int64_t waves = (ctas + slots - 1) / slots;
+            // fraction of SM slots busy over the run, slightly favouring fewer splits
+            const double eff = (double)ctas / (double)(waves * slots) - 0.002 * (double)sp;
+            if (eff > best + 1e-9) {
+                best = eff;
+                best_s = (int)sp;
+            }
+        }
+        split = best_s;
+    }
+    if (split > N) split = (int)std::max<int64_t>(1, N);
+    s.chunk = (N + split - 1) / split;
+    s.split = (int)((N + s.chunk - 1) / s.chunk);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lsp_default_options(lsp_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->sincos_mode = LSP_SINCOS_AUTO;
+    opt->phase_mode = LSP_PHASE_FIXED64;
+}
+
+lsp_status lsp_create(lsp_ctx** out, int device, const lsp_options* opt, void* cuda_stream) {
+    if (!out) return LSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return LSP_ERR_INVALID_ARG;
+    }
+    DeviceGuard guard(device);
+    lsp_ctx* ctx = new lsp_ctx();
+    ctx->device = device;
+    lsp_default_options(&ctx->opt);
+    if (opt) {
+        if (check_options(ctx, opt) != LSP_OK) {
+            delete ctx;
+            return LSP_ERR_INVALID_ARG;
+        }
+        ctx->opt = *opt;
+    }
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess && !cuda_stream) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->status_d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->status_d, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->status_h, sizeof(int));
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lsp_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? LSP_ERR_OOM : LSP_ERR_CUDA;
+    }
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    *out = ctx;
+    return LSP_OK;
+}
+
+lsp_status lsp_set_options(lsp_ctx* ctx, const lsp_options* opt) {
+    if (!ctx || !opt) return LSP_ERR_INVALID_ARG;
+    lsp_status st = check_options(ctx, opt);
+    if (st != LSP_OK) return st;
+    ctx->opt = *opt;
+    return LSP_OK;
+}
+
+lsp_status lsp_set_stream(lsp_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    if (!cuda_stream && !ctx->own_stream) {
+        DeviceGuard guard(ctx->device);
+        if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, LSP_ERR_CUDA, "cannot create stream");
+    }
+    ctx->stream = cuda_stream ? (cudaStream_t)cuda_stream : ctx->own_stream;
+    return LSP_OK;
+}
+
+lsp_status lsp_grid(double t_min, double t_max, int64_t N_t, double F_over, double F_high, double* f_0,
+                    double* df, int64_t* N_f) {
+    if (!f_0 || !df || !N_f) return LSP_ERR_INVALID_ARG;
+    const double span = t_max - t_min;
+    if (!(span > 0.0) || !std::isfinite(span) || !(F_over > 0.0) || !(F_high > 0.0) || N_t < 1)
+        return LSP_ERR_INVALID_ARG;
+    *df = 1.0 / (F_over * span);
+    *f_0 = *df;
+    *N_f = (int64_t)std::floor(F_high * F_over * (double)N_t / 2.0);
+    return LSP_OK;
+}
+
+lsp_status lsp_periodogram(lsp_ctx* ctx, const double* t, const double* X, int64_t N_t, double f_0,
+                           double df, int64_t N_f, float* P_out) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->timing_valid = false;
+    ctx->last_launches = 0;
+    if (N_t < 2) return fail(ctx, LSP_ERR_INVALID_ARG, "N_t = %lld: need at least 2 samples", (long long)N_t);
+    if (N_f < 0 || N_f >= (int64_t(1) << 31))
+        return fail(ctx, LSP_ERR_INVALID_ARG, "N_f = %lld out of range [0, 2^31)", (long long)N_f);
+    if (!std::isfinite(f_0) || !std::isfinite(df)) return fail(ctx, LSP_ERR_NONFINITE, "f_0 or df is not finite");
+    if (N_f == 0) return LSP_OK;
+    if (!t || !X || !P_out) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+
+    const bool t_dev = is_device_ptr(t), x_dev = is_device_ptr(X), p_dev = is_device_ptr(P_out);
+    const MainShape s = choose_shape(ctx, N_t, N_f);
+    lsp_status rs;
+    if ((rs = ensure(ctx, ctx->recA, (size_t)N_t * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->recB, (size_t)N_t * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->stats, sizeof(CurveStats))) != LSP_OK) return rs;
+    if (s.mode == 3 && (rs = ensure(ctx, ctx->recN, (size_t)N_t * 8)) != LSP_OK) return rs;
+    if (s.split > 1 && (rs = ensure(ctx, ctx->part, (size_t)s.split * 4 * (size_t)s.nf_pad * 4)) != LSP_OK)
+        return rs;
+    if (!t_dev && (rs = ensure(ctx, ctx->t_stage, (size_t)N_t * 8)) != LSP_OK) return rs;
+    if (!x_dev && (rs = ensure(ctx, ctx->x_stage, (size_t)N_t * 8)) != LSP_OK) return rs;
+    if (!p_dev && (rs = ensure(ctx, ctx->p_stage, (size_t)N_f * 4)) != LSP_OK) return rs;
+
+    const double* td = t;
+    const double* xd = X;
+    float* pd = p_dev ? P_out : (float*)ctx->p_stage.p;
+    if (!t_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(ctx->t_stage.p, t, (size_t)N_t * 8, cudaMemcpyHostToDevice, st));
+        td = (const double*)ctx->t_stage.p;
+    }
+    if (!x_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(ctx->x_stage.p, X, (size_t)N_t * 8, cudaMemcpyHostToDevice, st));
+        xd = (const double*)ctx->x_stage.p;
+    }
+    const bool timing = ctx->opt.timing != 0;
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+    CurveStats* stats = (CurveStats*)ctx->stats.p;
+    LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d, st));
+    LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
+                                           (uint4*)ctx->recA.p, (float4*)ctx->recB.p,
+                                           s.mode == 3 ? (float2*)ctx->recN.p : nullptr, st));
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+    LSP_CUDA(ctx, lsp::launch_main(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
+                                   (const float2*)ctx->recN.p, N_t, N_f, f_0, df, (float*)ctx->part.p, pd, st));
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
+    ctx->last_launches = 3;
+    if (s.split > 1) {
+        LSP_CUDA(ctx, lsp::launch_finalize(s, (const float*)ctx->part.p, N_t, N_f, pd, st));
+        ctx->last_launches = 4;
+    }
+    if (timing) {
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
+        ctx->timing_valid = true;
+        ctx->has_finalize = s.split > 1;
+    }
+    if (!p_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(P_out, pd, (size_t)N_f * 4, cudaMemcpyDeviceToHost, st));
+        return lsp_sync(ctx, -1.0);
+    }
+    return LSP_OK;
+}
+
+lsp_status lsp_sync(lsp_ctx* ctx, double timeout_s) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    DeviceGuard guard(ctx->device);
+    LSP_CUDA(ctx, cudaMemcpyAsync(ctx->status_h, ctx->status_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LSP_CUDA(ctx, cudaEventRecord(ctx->done, ctx->stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaEventQuery(ctx->done);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "cudaEventQuery");
+        if (timeout_s >= 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_s) return fail(ctx, LSP_ERR_TIMEOUT, "lsp_sync: %.3f s deadline passed", timeout_s);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    const int flags = *ctx->status_h;
+    if (flags) {
+        LSP_CUDA(ctx, cudaMemsetAsync(ctx->status_d, 0, sizeof(int), ctx->stream));
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flags & lsp::kStatusNonFinite) return fail(ctx, LSP_ERR_NONFINITE, "non-finite value in t or X");
+        return fail(ctx, LSP_ERR_DEGENERATE, "X has zero variance");
+    }
+    return LSP_OK;
+}
+
+lsp_status lsp_last_timing(lsp_ctx* ctx, float* ms_prep, float* ms_main, float* ms_finalize) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    if (!ctx->timing_valid) return fail(ctx, LSP_ERR_INVALID_ARG, "no timed call (set the timing option)");
+    LSP_CUDA(ctx, cudaEventSynchronize(ctx->ev[3]));
+    float a = 0, b = 0, c = 0;
+    LSP_CUDA(ctx, cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+    LSP_CUDA(ctx, cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+    LSP_CUDA(ctx, cudaEventElapsedTime(&c, ctx->ev[2], ctx->ev[3]));
+    if (ms_prep) *ms_prep = a;
+    if (ms_main) *ms_main = b;
+    if (ms_finalize) *ms_finalize = ctx->has_finalize ? c : 0.f;
+    return LSP_OK;
+}
+
+int32_t lsp_last_launch_count(const lsp_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+const char* lsp_last_error(const lsp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void lsp_destroy(lsp_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    DevBuf* bufs[] = {&ctx->recA, &ctx->recB, &ctx->recN, &ctx->part, &ctx->stats,
+                      &ctx->t_stage, &ctx->x_stage, &ctx->p_stage};
+    for (DevBuf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->status_d) cudaFree(ctx->status_d);
+    if (ctx->status_h) cudaFreeHost(ctx->status_h);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->done) cudaEventDestroy(ctx->done);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

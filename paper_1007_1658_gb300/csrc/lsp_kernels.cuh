@@ -1,0 +1,69 @@
+// lsp_kernels.cuh -- internal declarations shared by the library's .cu files.
+// Nothing here is part of the public ABI (include/lsp.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsp {
+
+// Device status bits, OR-ed into a context-owned word by the kernels.
+enum : int {
+    kStatusNonFinite = 1,
+    kStatusDegenerate = 2,
+};
+
+// Per-curve statistics written by prep_stats (Sec. 3 normalization, FP64).
+struct CurveStats {
+    double mean;     // mean of X
+    double inv_sd;   // 1/sqrt(population variance); NaN when degenerate
+    double t_ref;    // earliest sample time (phase origin)
+    double pad;
+};
+
+// Phase records of one sample, 32 bytes, consumed by the main kernels.
+//   A = {u_lo, u_hi, v_lo, v_hi}: u = frac(t' df), v = frac(t' f0) + offsets,
+//       both as 64-bit fixed-point turns (t' = t - t_ref).
+//   B = {x_hat, cos 2 pi u, sin 2 pi u, bits of round(u / 2^32)}.
+// The offsets folded into v: 2^63 (half a turn, so that the bit-trick angle
+// below lands on the true phase), 2^31 (round the top word) and 2^40 (round
+// the 23-bit mantissa taken from the top word).
+constexpr uint64_t kPhaseOffset = (1ull << 63) + (1ull << 40) + (1ull << 31);
+
+// Kernel launchers (all asynchronous on `st`).
+// Curves are given in CSR form: samples of curve c are [off[c], off[c+1]).
+// When off == nullptr there is one curve of n0 samples.
+cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
+                              int n_curves, CurveStats* stats, int* status, cudaStream_t st);
+
+cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
+                                int n_curves, int64_t max_n, const double* f0, const double* df,
+                                double f0_single, double df_single, const CurveStats* stats,
+                                uint4* recA, float4* recB, float2* recN, cudaStream_t st);
+
+struct MainShape {
+    int mode;      // 1 = MUFU, 2 = RECUR, 3 = NAIVE_FP32
+    int F;         // adjacent frequencies per thread
+    int split;     // N_t chunks per frequency block
+    int64_t chunk; // samples per chunk
+    int nfb;       // frequency blocks
+    int64_t nf_pad;// padded row length of the partial-sum workspace
+};
+
+constexpr int kMainThreads = 128;
+constexpr int kTile = 256;
+
+// Frequencies covered by one CTA of the main kernel.
+inline int freqs_per_block(int F) { return kMainThreads * F; }
+
+// Resident CTAs per SM of the main kernel for (mode, F).
+int main_occupancy(int mode, int F);
+
+cudaError_t launch_main(const MainShape& s, const uint4* recA, const float4* recB, const float2* recN,
+                        int64_t N, int64_t N_f, double f0, double df, float* part, float* P_out,
+                        cudaStream_t st);
+
+cudaError_t launch_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f,
+                            float* P_out, cudaStream_t st);
+
+}  // namespace lsp

@@ -1,0 +1,161 @@
+// prep.cu -- per-curve normalization and per-sample phase records.
+//
+// The only FP64 arithmetic on the GPU lives here: the mean and population
+// variance of X (Sec. 3: the series is shifted to zero mean and scaled to
+// unit variance) and the exact fixed-point phases frac(t' df), frac(t' f0)
+// that replace the single-precision range reduction of Sec. 4.3.
+#include <cfloat>
+#include <cmath>
+
+#include "lsp_kernels.cuh"
+
+namespace lsp {
+namespace {
+
+constexpr int kStatsThreads = 512;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum / min; the result is valid in every thread.
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) sh[32] = r;
+    __syncthreads();
+    return sh[32];
+}
+
+__device__ double block_min(double v, double* sh) {
+    v = warp_min(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : DBL_MAX;
+    if (w == 0) r = warp_min(r);
+    if (threadIdx.x == 0) sh[32] = r;
+    __syncthreads();
+    return sh[32];
+}
+
+// One CTA per curve: t_ref = min t, mean and population variance of X in
+// two passes, non-finite detection.  A degenerate curve gets inv_sd = NaN, so
+// its periodogram comes out NaN and the status word says why.
+__global__ void __launch_bounds__(kStatsThreads)
+prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
+                  const int64_t* __restrict__ off, int64_t n0, CurveStats* __restrict__ stats,
+                  int* __restrict__ status) {
+    __shared__ double sh[33];
+    const int c = blockIdx.x;
+    const int64_t b = off ? off[c] : 0;
+    const int64_t e = off ? off[c + 1] : n0;
+    const int64_t n = e - b;
+    double s = 0.0, tmin = DBL_MAX;
+    int bad = 0;
+    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const double x = X[j], tj = t[j];
+        bad |= !(isfinite(x) && isfinite(tj));
+        s += x;
+        tmin = fmin(tmin, tj);
+    }
+    bad = __syncthreads_or(bad);
+    s = block_sum(s, sh);
+    tmin = block_min(tmin, sh);
+    const double mean = s / (double)n;
+    double v = 0.0;
+    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
+        const double d = X[j] - mean;
+        v = fma(d, d, v);
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        const double var = v / (double)n;
+        const bool ok = !bad && var > 0.0 && n >= 2;
+        CurveStats r;
+        r.mean = mean;
+        r.inv_sd = ok ? 1.0 / sqrt(var) : __longlong_as_double(0x7ff8000000000000ll);
+        r.t_ref = bad ? 0.0 : tmin;
+        r.pad = var;
+        stats[c] = r;
+        if (bad) atomicOr(status, kStatusNonFinite);
+        else if (!ok) atomicOr(status, kStatusDegenerate);
+    }
+}
+
+// frac(a*b) as a 64-bit fixed-point number of turns, exact to ~1 unit of 2^-64:
+// the product is split into p + e exactly (Dekker/Ogita-Rump-Oishi TwoProduct
+// through fma), floor(p) is removed exactly, and both pieces are scaled by
+// 2^64 and added modulo 2^64.  Requires |a*b| < 2^52.
+__device__ __forceinline__ uint64_t frac_turns64(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    const double e = fma(a, b, -p);
+    const double fr = p - floor(p);
+    const uint64_t U = __double2ull_rn(fr * 0x1p64);
+    const int64_t E = __double2ll_rn(e * 0x1p64);
+    return U + (uint64_t)E;
+}
+
+__global__ void __launch_bounds__(256)
+prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
+                    const int64_t* __restrict__ off, int64_t n0,
+                    const double* __restrict__ f0a, const double* __restrict__ dfa,
+                    double f0s, double dfs, const CurveStats* __restrict__ stats,
+                    uint4* __restrict__ recA, float4* __restrict__ recB, float2* __restrict__ recN) {
+    const int c = blockIdx.y;
+    const int64_t b = off ? off[c] : 0;
+    const int64_t e = off ? off[c + 1] : n0;
+    const CurveStats st = stats[c];
+    const double f0 = f0a ? f0a[c] : f0s;
+    const double df = dfa ? dfa[c] : dfs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < e; j += stride) {
+        const double tt = t[j] - st.t_ref;
+        const uint64_t u = frac_turns64(tt, df);
+        const uint64_t v = frac_turns64(tt, f0) + kPhaseOffset;
+        const uint32_t du = (uint32_t)((u + (1ull << 31)) >> 32);
+        // rotation of one grid step, cos/sin(2 pi u), from the exact fixed-point turn
+        const double turn = (double)(int64_t)u * 0x1p-64;
+        double sn, cs;
+        sincospi(2.0 * turn, &sn, &cs);
+        const float xh = (float)((X[j] - st.mean) * st.inv_sd);
+        recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
+        recB[j] = make_float4(xh, (float)cs, (float)sn, __uint_as_float(du));
+        if (recN) recN[j] = make_float2(xh, __double2float_rn(tt));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
+                              int n_curves, CurveStats* stats, int* status, cudaStream_t st) {
+    prep_stats_kernel<<<n_curves, kStatsThreads, 0, st>>>(t, X, off, n0, stats, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
+                                int n_curves, int64_t max_n, const double* f0, const double* df,
+                                double f0_single, double df_single, const CurveStats* stats,
+                                uint4* recA, float4* recB, float2* recN, cudaStream_t st) {
+    int64_t bx = (max_n + 255) / 256;
+    if (bx > 4096) bx = 4096;
+    if (bx < 1) bx = 1;
+    dim3 grid((unsigned)bx, (unsigned)n_curves);
+    prep_records_kernel<<<grid, 256, 0, st>>>(t, X, off, n0, f0, df, f0_single, df_single, stats,
+                                              recA, recB, recN);
+    return cudaGetLastError();
+}
+
+}  // namespace lsp

@@ -1,0 +1,200 @@
+"""ctypes binding of ``liblsp.so`` (include/lsp.h), argument marshalling only.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed to
+the C ABI as raw pointers.  Device tensors go through the library's
+asynchronous device path on the current torch stream (or the stream given to
+``Context``); host arrays go through its host path, which copies them in and
+the result out.  Every step of the computation runs in the library's CUDA
+kernels.  If the library has not been built, loading fails loudly: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsp.so")
+_lib = None
+_lock = threading.Lock()
+
+OK, ERR_INVALID_ARG, ERR_DEGENERATE, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_MODEL, \
+    ERR_UNSUPPORTED = range(9)
+SINCOS_AUTO, SINCOS_MUFU, SINCOS_RECUR = 0, 1, 2
+PHASE_FIXED64, PHASE_NAIVE_FP32 = 0, 1
+
+_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "DEGENERATE", 3: "NONFINITE", 4: "OOM", 5: "CUDA",
+          6: "TIMEOUT", 7: "NO_MODEL", 8: "UNSUPPORTED"}
+
+
+class LspError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class lsp_options(ctypes.Structure):
+    _fields_ = [("sincos_mode", ctypes.c_int32), ("phase_mode", ctypes.c_int32),
+                ("freqs_per_thread", ctypes.c_int32), ("split", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+def load():
+    """Open liblsp.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblsp.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        p, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        lib.lsp_default_options.argtypes = [ctypes.POINTER(lsp_options)]
+        lib.lsp_default_options.restype = None
+        lib.lsp_create.argtypes = [ctypes.POINTER(p), ctypes.c_int, ctypes.POINTER(lsp_options), p]
+        lib.lsp_set_options.argtypes = [p, ctypes.POINTER(lsp_options)]
+        lib.lsp_set_stream.argtypes = [p, p]
+        lib.lsp_periodogram.argtypes = [p, p, p, i64, d, d, i64, p]
+        lib.lsp_grid.argtypes = [d, d, i64, d, d, p, p, p]
+        lib.lsp_sync.argtypes = [p, d]
+        lib.lsp_last_timing.argtypes = [p, p, p, p]
+        lib.lsp_last_launch_count.argtypes = [p]
+        lib.lsp_last_launch_count.restype = i32
+        lib.lsp_last_error.argtypes = [p]
+        lib.lsp_last_error.restype = ctypes.c_char_p
+        lib.lsp_destroy.argtypes = [p]
+        lib.lsp_destroy.restype = None
+        for name in ("lsp_create", "lsp_set_options", "lsp_set_stream", "lsp_periodogram", "lsp_grid",
+                     "lsp_sync", "lsp_last_timing"):
+            getattr(lib, name).restype = ctypes.c_int
+        _extra_prototypes(lib)
+        _lib = lib
+        return lib
+
+
+def _extra_prototypes(lib):
+    """Prototypes of entry points added beside the single-curve path."""
+    p, i32, i64, d, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    if hasattr(lib, "lsp_batch"):
+        lib.lsp_batch.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
+        lib.lsp_batch.restype = ctypes.c_int
+
+
+def options(**kw) -> lsp_options:
+    o = lsp_options()
+    load().lsp_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, int(v))
+    return o
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(a))
+
+
+class Context:
+    """Owns an lsp_ctx.  ``stream``: a torch.cuda.Stream, a raw cudaStream_t
+    (int), or None for the current torch stream at each call."""
+
+    def __init__(self, device: int = 0, stream=None, **opts):
+        self._lib = load()
+        self.device = int(device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        o = options(**opts)
+        st = self._lib.lsp_create(ctypes.byref(h), self.device, ctypes.byref(o), self._raw_stream())
+        if st != OK:
+            raise LspError(st, "lsp_create failed")
+        self.h = h
+
+    def _raw_stream(self):
+        s = self._stream
+        if s is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+            except Exception:
+                pass
+            return None
+        if hasattr(s, "cuda_stream"):
+            return ctypes.c_void_p(s.cuda_stream)
+        return ctypes.c_void_p(int(s))
+
+    def _check(self, st):
+        if st != OK:
+            raise LspError(st, self._lib.lsp_last_error(self.h).decode())
+
+    def _bind_stream(self):
+        self._check(self._lib.lsp_set_stream(self.h, self._raw_stream()))
+
+    def set_options(self, **opts):
+        o = options(**opts)
+        self._check(self._lib.lsp_set_options(self.h, ctypes.byref(o)))
+
+    def periodogram(self, t, X, f0, df, nf, out=None):
+        """P[k] = P_n(f0 + k df), k < nf (Eq. 1-2 via Eq. 5-8)."""
+        nf = int(nf)
+        if out is None:
+            if hasattr(t, "data_ptr"):
+                import torch
+                out = torch.empty(nf, dtype=torch.float32, device=t.device)
+            else:
+                out = np.empty(nf, dtype=np.float32)
+        self._bind_stream()
+        n = t.numel() if hasattr(t, "numel") else t.size
+        self._check(self._lib.lsp_periodogram(self.h, _ptr(t), _ptr(X), int(n), float(f0), float(df), nf,
+                                              _ptr(out)))
+        return out
+
+    def sync(self, timeout_s: float = -1.0):
+        self._check(self._lib.lsp_sync(self.h, float(timeout_s)))
+
+    def last_timing(self):
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        self._check(self._lib.lsp_last_timing(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def last_launch_count(self) -> int:
+        return int(self._lib.lsp_last_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lsp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def grid(t_min, t_max, n, f_over, f_high):
+    """Eq. 9-11 grid: (f0, df, nf) with f0 = df."""
+    f0, df, nf = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    st = load().lsp_grid(float(t_min), float(t_max), int(n), float(f_over), float(f_high),
+                         ctypes.byref(f0), ctypes.byref(df), ctypes.byref(nf))
+    if st != OK:
+        raise LspError(st, "lsp_grid")
+    return f0.value, df.value, nf.value
