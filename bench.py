@@ -184,6 +184,8 @@ def run_gpu(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     c = synth.gapped_100k()
+    if args.nf:
+        c.nf = int(args.nf)  # smaller case of the same kernel (profiling captures)
     f0 = c.f0 + rank * c.nf * c.df  # this rank's block of the grid
     terms = c.t.size * c.nf
     t_d = torch.from_numpy(c.t).to(dev)
@@ -225,18 +227,9 @@ def run_gpu(args, rank, world, dist):
     value = world * terms * args.steps / (total_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (copies inside)
-    t_h = torch.from_numpy(c.t).pin_memory()
-    X_h = torch.from_numpy(c.X).pin_memory()
-    P_h = torch.empty(c.nf, dtype=torch.float32).pin_memory()
-    ctx_h = lsp.Context(local, stream=stream, sincos_mode=args.mode)
-    ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)
-    e2e_s = []
-    for _ in range(max(3, args.steps // 2)):
-        t0 = time.perf_counter()
-        ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)  # blocks until P_h is written
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_val = world * terms * len(e2e_s) / sum(e2e_s)
-    ctx_h.close()
+    e2e_val = None
+    if args.e2e:
+        e2e_val = _e2e(lsp, torch, c, f0, local, stream, args, world)
 
     if rank != 0:
         ctx.close()
@@ -261,8 +254,9 @@ def run_gpu(args, rank, world, dist):
                          "FMA pipe, 8 FP32 ops/term" if mode == lsp.SINCOS_RECUR else "SFU, 2 MUFU ops/term",
                          terms_per_clk, sms, peaks["sm_max_mhz"], peak_src),
                      "main_ms": float(np.mean(main_ms))},
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c.t.nbytes + c.X.nbytes),
-                "d2h_bytes_per_step": int(c.nf * 4)},
+        "e2e": None if e2e_val is None else {
+            "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c.t.nbytes + c.X.nbytes),
+            "d2h_bytes_per_step": int(c.nf * 4)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -273,6 +267,24 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def _e2e(lsp, torch, c, f0, local, stream, args, world):
+    """Same metric through the C ABI with pinned host buffers: every step copies
+    t and X in and P out inside the timed region (the call blocks on P)."""
+    terms = c.t.size * c.nf
+    t_h = torch.from_numpy(c.t).pin_memory()
+    X_h = torch.from_numpy(c.X).pin_memory()
+    P_h = torch.empty(c.nf, dtype=torch.float32).pin_memory()
+    ctx_h = lsp.Context(local, stream=stream, sincos_mode=args.mode)
+    ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)
+    e2e_s = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)  # blocks until P_h is written
+        e2e_s.append(time.perf_counter() - t0)
+    ctx_h.close()
+    return world * terms * len(e2e_s) / sum(e2e_s)
 
 
 def run_batch_bench(ctx, torch, dev, stream, args):
@@ -292,6 +304,8 @@ def main():
     ap.add_argument("--cpu-bins", type=int, default=16384, help="cpu_baseline: oracle frequencies (~10-30 s)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--nf", type=int, default=0, help="override N_f (smaller profiling case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
