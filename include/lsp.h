@@ -142,6 +142,33 @@ const char *lsp_last_error(const lsp_ctx *ctx);
 /* Release the context, its stream (if owned) and its workspace.  NULL is a no-op. */
 void lsp_destroy(lsp_ctx *ctx);
 
+/*
+ * Allocation-free variant of lsp_periodogram.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they run -- e.g. an application whose memory pool already owns the
+ * whole GPU, or a latency-critical loop that cannot afford cudaMalloc's
+ * device-wide synchronization.  It computes the same P_out[k] = P_n(f_0 + k df)
+ * (recurrence sin/cos, fixed-point phase) without a context and without any
+ * cudaMalloc/cudaFree or allocating library call.
+ *
+ * Scratch: one file-scope device array of 64 MiB + 256 B that every GPU which
+ * loads the library holds until the process exits.  Limit: 2 <= N_t <= 524,288
+ * (larger N_t returns LSP_ERR_INVALID_ARG); N_f < 2^31 as for lsp_periodogram.
+ * t, X and P_out must be device pointers on the current device (else
+ * INVALID_ARG); the work is queued on `cuda_stream` (NULL: the legacy default
+ * stream) and the call returns without waiting.  The first call on a device,
+ * with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialized by the caller.  Data errors
+ * found on the device (non-finite input, zero variance) are not reported by
+ * status: they show as NaN in P_out.
+ * Errors: INVALID_ARG, NONFINITE (f_0/df), CUDA.
+ */
+lsp_status lsp_periodogram_noalloc(const double *t, const double *X, int64_t N_t, double f_0,
+                                   double df, int64_t N_f, float *P_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

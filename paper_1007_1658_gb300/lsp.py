@@ -78,6 +78,9 @@ def load():
 def _extra_prototypes(lib):
     """Prototypes of entry points added beside the single-curve path."""
     p, i32, i64, d, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    if hasattr(lib, "lsp_periodogram_noalloc"):
+        lib.lsp_periodogram_noalloc.argtypes = [p, p, i64, d, d, i64, p, p]
+        lib.lsp_periodogram_noalloc.restype = ctypes.c_int
     if hasattr(lib, "lsp_batch"):
         lib.lsp_batch.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
         lib.lsp_batch.restype = ctypes.c_int
@@ -188,6 +191,23 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+def periodogram_noalloc(t, X, f0, df, nf, out, stream=None):
+    """lsp_periodogram_noalloc: device tensors only, no context, nothing allocated
+    by the library (the caller provides `out`).  Queued on `stream` (a
+    torch.cuda.Stream or raw handle; None = current torch stream)."""
+    lib = load()
+    if stream is None:
+        import torch
+        raw = torch.cuda.current_stream().cuda_stream
+    else:
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = lib.lsp_periodogram_noalloc(_ptr(t), _ptr(X), int(t.numel()), float(f0), float(df), int(nf), _ptr(out),
+                                     ctypes.c_void_p(raw))
+    if st != OK:
+        raise LspError(st, "lsp_periodogram_noalloc")
+    return out
 
 
 def grid(t_min, t_max, n, f_over, f_high):
