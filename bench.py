@@ -193,7 +193,7 @@ def run_gpu(args, rank, world, dist):
     P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.Stream(device=dev)
-    ctx = lsp.Context(local, stream=stream, timing=1, sincos_mode=args.mode)
+    ctx = lsp.Context(local, stream=stream, timing=1, sincos_mode=args.mode, freqs_per_thread=args.F)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             ctx.periodogram(t_d, X_d, f0, c.df, c.nf, out=P_d)
@@ -276,7 +276,7 @@ def _e2e(lsp, torch, c, f0, local, stream, args, world):
     t_h = torch.from_numpy(c.t).pin_memory()
     X_h = torch.from_numpy(c.X).pin_memory()
     P_h = torch.empty(c.nf, dtype=torch.float32).pin_memory()
-    ctx_h = lsp.Context(local, stream=stream, sincos_mode=args.mode)
+    ctx_h = lsp.Context(local, stream=stream, sincos_mode=args.mode, freqs_per_thread=args.F)
     ctx_h.periodogram(t_h, X_h, f0, c.df, c.nf, out=P_h)
     e2e_s = []
     for _ in range(max(3, args.steps // 2)):
@@ -299,7 +299,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--mode", type=int, default=0, help="sin/cos mode: 0 auto, 1 MUFU, 2 recurrence")
+    ap.add_argument("--mode", type=int, default=0,
+                    help="sin/cos mode: 0 auto, 1 MUFU, 2 recurrence, 3 three-term recurrence")
+    ap.add_argument("--F", type=int, default=0, help="frequencies per thread (0 = auto)")
     ap.add_argument("--ref-bins", type=int, default=2048, help="reference arm: oracle frequencies per step")
     ap.add_argument("--cpu-bins", type=int, default=16384, help="cpu_baseline: oracle frequencies (~10-30 s)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -50,10 +50,13 @@ typedef enum lsp_status {
 
 /* How sin/cos of the phase are produced in the O(N_t N_f) loop. */
 typedef enum lsp_sincos_mode {
-    LSP_SINCOS_AUTO = 0,   /* the library's choice (currently RECUR)                     */
+    LSP_SINCOS_AUTO = 0,   /* the library's choice (currently RECUR3)                    */
     LSP_SINCOS_MUFU = 1,   /* hardware sin/cos (SFU) of every phase (Sec. 4.3's choice)  */
-    LSP_SINCOS_RECUR = 2   /* SFU seed per strip of adjacent frequencies, then the
+    LSP_SINCOS_RECUR = 2,  /* SFU seed per strip of adjacent frequencies, then the
                               angle-addition rotation by (cos, sin)(2 pi t_j df) on FMA */
+    LSP_SINCOS_RECUR3 = 3  /* SFU seed, one rotation, then the three-term form
+                              z_{k+1} = 2 cos(2 pi t_j df) z_k - z_{k-1} (half the FMA work
+                              of RECUR; error grows faster with the strip length)      */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */
@@ -67,7 +70,7 @@ typedef enum lsp_phase_mode {
 typedef struct lsp_options {
     int32_t sincos_mode;      /* lsp_sincos_mode                                       */
     int32_t phase_mode;       /* lsp_phase_mode                                        */
-    int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|16 */
+    int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|16|24 */
     int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t reserved[7];      /* must be zero                                          */
@@ -109,6 +112,48 @@ lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64
                            double f_0, double df, int64_t N_f, float *P_out);
 
 /*
+ * Many periodograms in one call: measured curves, or Monte-Carlo noise
+ * realizations of sampling patterns (Sec. 6.2: the distribution of peak
+ * heights under pure noise, e.g. the number of independent frequencies that
+ * Eq. 3's exponent should be).  One persistent kernel takes work items
+ * (realization, curve, block of frequencies) longest curve first; the whole
+ * batch runs as one CUDA graph, cached and replayed while the arguments'
+ * pointers and metadata stay the same (a new seed needs no new graph).
+ *
+ * n_curves in [1, 65535]; curve c has samples t[t_off[c] .. t_off[c+1]) (FP64,
+ * t_off[0] = 0, at least 2 samples per curve) and its own grid
+ * f_0[c] + k df[c], k < N_f[c] (0 <= N_f[c] < 2^31).
+ * X: measurements in the same layout (n_real must then be 1), or NULL for
+ *   noise: realization r of curve c, sample j, is N(0,1) from Philox-4x32-10
+ *   with counter (j/4, c, r, 0) and key `seed` (see lsp_noise), normalized
+ *   per realization like measured data (Sec. 3).  n_real in [1, 65535].
+ * P_out (optional): P of realization r, curve c, bin k at
+ *   P_out[r * P_off[n_curves] + P_off[c] + k]; P_off[c+1] - P_off[c] >= N_f[c].
+ * maxP_out, argmax_out (optional, [n_real * n_curves], index r * n_curves + c):
+ *   the largest P of each periodogram and its bin k (lowest k on ties; -1 and
+ *   0 for a curve with N_f = 0).
+ * At least one output must be given.  Arrays may be host or device pointers
+ * (metadata is read on the host in either case); the sin/cos mode and strip
+ * length follow the context's options (the naive FP32 phase is not offered).
+ * Errors: INVALID_ARG, NONFINITE (grid; t/X on the device), DEGENERATE
+ * (measured X with zero variance, on the device), UNSUPPORTED, OOM, CUDA.
+ */
+lsp_status lsp_batch(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, const double *t,
+                     const double *X, uint64_t seed, int32_t n_real, const double *f_0,
+                     const double *df, const int64_t *N_f, float *P_out, const int64_t *P_off,
+                     float *maxP_out, int32_t *argmax_out);
+
+/*
+ * The raw N(0,1) noise lsp_batch draws for (seed, curve, realization), samples
+ * 0..N-1, before normalization: Philox-4x32-10 (Salmon et al. 2011) block
+ * j/4 with counter (j/4, curve, real, 0) and key (seed low word, seed high
+ * word); each word w gives u = (2 (w >> 9) + 1) 2^-24, and Box-Muller turns
+ * (u0, u1), (u2, u3) into sqrt(-2 ln u_a) (cos, sin)(2 pi u_b).  out[N] FP32,
+ * host or device.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+lsp_status lsp_noise(lsp_ctx *ctx, uint64_t seed, int32_t curve, int32_t real, int64_t N, float *out);
+
+/*
  * Grid helper, Eq. 10-11 with Eq. 9's origin: df = 1/(F_over (t_max - t_min)),
  * N_f = floor(F_high F_over N_t / 2), f_0 = df.  Host-only arithmetic.
  * Errors: INVALID_ARG (t_max <= t_min, F_over <= 0, F_high <= 0, N_t < 1).
@@ -148,10 +193,10 @@ void lsp_destroy(lsp_ctx *ctx);
  * while they run -- e.g. an application whose memory pool already owns the
  * whole GPU, or a latency-critical loop that cannot afford cudaMalloc's
  * device-wide synchronization.  It computes the same P_out[k] = P_n(f_0 + k df)
- * (recurrence sin/cos, fixed-point phase) without a context and without any
+ * (three-term recurrence sin/cos, fixed-point phase) without a context and without any
  * cudaMalloc/cudaFree or allocating library call.
  *
- * Scratch: one file-scope device array of 64 MiB + 256 B that every GPU which
+ * Scratch: one file-scope device array of 64 MiB + 8 KiB that every GPU which
  * loads the library holds until the process exits.  Limit: 2 <= N_t <= 524,288
  * (larger N_t returns LSP_ERR_INVALID_ARG); N_f < 2^31 as for lsp_periodogram.
  * t, X and P_out must be device pointers on the current device (else

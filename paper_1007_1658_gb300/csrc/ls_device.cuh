@@ -1,0 +1,180 @@
+// ls_device.cuh -- device-side pieces of the O(N_t N_f) evaluation shared by
+// the single-curve kernels (ls_main.cu) and the batched Monte-Carlo kernel
+// (batch.cu): phase handling, the per-sample update of one frequency strip
+// in each sin/cos mode, the cp.async tile pipeline and Eq. 5-6.
+#pragma once
+
+#include <cstdint>
+
+#include "lsp_kernels.cuh"
+
+namespace lsp {
+namespace dev {
+
+constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kThreePi = 9.42477796076937971538f;
+
+// Internal kernel modes (the kMode* values of lsp_kernels.cuh).
+enum : int { kMufu = kModeMufu, kRecur = kModeRecur, kNaive = kModeNaive, kRecur3 = kModeRecur3 };
+
+// Top 23 bits of a 32-bit turn fraction, offset by half a turn at prep time,
+// become a float in [1, 2) by pasting them under the exponent of 1.0; one FMA
+// maps that to an angle in [-pi, pi).  No int->float conversion unit is used.
+__device__ __forceinline__ float phase_to_angle(uint32_t p) {
+    return fmaf(__uint_as_float(0x3F800000u | (p >> 9)), kTwoPi, -kThreePi);
+}
+
+// Top 32 bits of the phase v + k u (mod 2^64) of record A at frequency k.
+__device__ __forceinline__ uint32_t top_phase(const uint4& A, uint32_t k) {
+    const uint64_t u = ((uint64_t)A.y << 32) | A.x;
+    const uint64_t v = ((uint64_t)A.w << 32) | A.z;
+    return (uint32_t)((v + (uint64_t)k * u) >> 32);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Eq. 5 with tau from Eq. 6, in closed form.  With A = CC - SS = 2CC - N,
+// B = 2CS and R = |A + iB| = |sum exp(2 i w t_j)|, tan 2wtau = B/A gives
+// cos 2wtau = A/R, sin 2wtau = B/R, and the two denominators of Eq. 5 are
+// (N + R)/2 and (N - R)/2; the two numerators are (|Z|^2 +- Re(e^{-2iwtau} Z^2))/2
+// with Z = XC + i XS.  No trig, and R = 0 (tau undefined) takes wtau = 0.
+// A term whose denominator is below N 2^-16 is taken as zero.
+__device__ __forceinline__ float periodogram_value(float XC, float XS, float CC, float CS, float n) {
+    const float A = 2.f * CC - n;
+    const float B = 2.f * CS;
+    const float R = sqrtf(A * A + B * B);
+    float c2 = 1.f, s2 = 0.f;
+    if (R > 0.f) {
+        c2 = A / R;
+        s2 = B / R;
+    }
+    const float z2 = XC * XC + XS * XS;
+    const float cross = c2 * (XC * XC - XS * XS) + s2 * (2.f * XC * XS);
+    const float num1 = fmaxf(0.5f * (z2 + cross), 0.f);
+    const float num2 = fmaxf(0.5f * (z2 - cross), 0.f);
+    const float den1 = 0.5f * (n + R);
+    const float den2 = 0.5f * (n - R);
+    const float thr = n * (1.f / 65536.f);
+    float P = 0.f;
+    if (den1 > thr) P += num1 / den1;
+    if (den2 > thr) P += num2 / den2;
+    return 0.5f * P;
+}
+
+// The four running sums of Eq. 8 for a strip of F adjacent frequencies
+// k0 .. k0+F-1 of one thread.
+template <int F, int MODE>
+struct Strip {
+    float xc[F], xs[F], cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) xc[i] = xs[i] = cc[i] = cs[i] = 0.f;
+    }
+
+    __device__ __forceinline__ void acc(int i, float x, float c, float s) {
+        xc[i] = fmaf(x, c, xc[i]);
+        xs[i] = fmaf(x, s, xs[i]);
+        cc[i] = fmaf(c, c, cc[i]);
+        cs[i] = fmaf(c, s, cs[i]);
+    }
+
+    // Sample with phase record A = {u, v}, B = {x_hat, cos 2 pi u, sin 2 pi u,
+    // round(u / 2^32)} and normalized value x.
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, uint32_t k0) {
+        uint32_t p = top_phase(A, k0);
+        if (MODE == kMufu) {
+            const uint32_t du = __float_as_uint(B.w);
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float s, c;
+                __sincosf(phase_to_angle(p), &s, &c);
+                acc(i, x, c, s);
+                p += du;
+            }
+        } else {
+            // seed from the exact phase, then step k -> k+1 by the rotation
+            // (cos, sin)(2 pi u): RECUR uses the angle-addition formulas at
+            // every step; RECUR3 uses them once and then the three-term form
+            // z_{i+1} = 2 cos(2 pi u) z_i - z_{i-1}.
+            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            float s, c;
+            __sincosf(phase_to_angle(p), &s, &c);
+            float cp = c, sp = s;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                acc(i, x, c, s);
+                if (i + 1 < F) {
+                    float cn, sn;
+                    if (MODE == kRecur || i == 0) {
+                        cn = fmaf(c, C, -s * S);
+                        sn = fmaf(s, C, c * S);
+                    } else {
+                        cn = fmaf(C2, c, -cp);
+                        sn = fmaf(C2, s, -sp);
+                    }
+                    cp = c;
+                    sp = s;
+                    c = cn;
+                    s = sn;
+                }
+            }
+        }
+    }
+};
+
+// Double-buffered cp.async pipeline over the samples [j0, j1) in tiles of
+// kTile: stages the two 16-byte phase records of every sample and, when
+// `xr` is given, the sample values from that array; calls
+// body(a, b, x_or_null, n) once per tile with the tile in shared memory.
+// Every thread of the CTA must call it (it synchronizes the CTA).
+template <bool XARR>
+struct TileSmem {
+    uint4 A[2][kTile];
+    float4 B[2][kTile];
+    float X[2][XARR ? kTile : 1];
+};
+
+template <bool XARR, class Body>
+__device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* __restrict__ recA,
+                                              const float4* __restrict__ recB, const float* __restrict__ xr,
+                                              int64_t j0, int64_t j1, Body&& body) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntiles = j1 > j0 ? (int)((j1 - j0 + kTile - 1) / kTile) : 0;
+    auto stage = [&](int buf, int64_t jt) {
+        const int n = (int)min((int64_t)kTile, j1 - jt);
+        for (int q = tid; q < n; q += nt) {
+            cp_async16(&sm.A[buf][q], recA + jt + q);
+            cp_async16(&sm.B[buf][q], recB + jt + q);
+            if (XARR) cp_async4(&sm.X[buf][q], xr + jt + q);
+        }
+    };
+    if (ntiles > 0) stage(0, j0);
+    cp_async_commit();
+    for (int it = 0; it < ntiles; ++it) {
+        const int64_t jt = j0 + (int64_t)it * kTile;
+        if (it + 1 < ntiles) stage((it + 1) & 1, jt + kTile);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int n = (int)min((int64_t)kTile, j1 - jt);
+        body(sm.A[it & 1], sm.B[it & 1], XARR ? sm.X[it & 1] : nullptr, n);
+        __syncthreads();
+    }
+}
+
+}  // namespace dev
+}  // namespace lsp

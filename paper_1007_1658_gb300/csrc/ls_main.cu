@@ -1,5 +1,5 @@
 // ls_main.cu -- the O(N_t N_f) evaluation of the sums of Eq. 8 and the
-// periodogram of Eq. 5-6.
+// periodogram of Eq. 5-6 for one curve.
 //
 // Layout of the work: a CTA of kMainThreads threads owns kMainThreads*F
 // adjacent grid frequencies (each thread a strip of F adjacent k) and one
@@ -15,76 +15,31 @@
 //
 // Phase (exact): the records hold u = frac(t' df) and v = frac(t' f0) as
 // 64-bit fixed-point turns; for frequency k the phase is v + k u mod 2^64.
-// A thread forms the top 32 bits once per sample for its first k and then
-// steps by round(u / 2^32) (error <= F/2 units of 2^-32 turn), so the
+// A thread forms the top 32 bits once per sample for its first k, so the
 // phase never loses accuracy however large f t grows.
 //
-// sin/cos, two modes:
-//   MUFU  -- every (j, k) takes the hardware sin/cos of the phase (the
-//            paper's __sincosf, Sec. 4.3): 2 SFU ops per term.
-//   RECUR -- the hardware sin/cos seeds the first k of the strip; the next
-//            F-1 follow from the angle-addition formulas with the per-sample
-//            rotation (cos, sin)(2 pi u_j): 4 FMA-pipe ops per term.  The
-//            recurrence (the trig recursion of Sec. 3, there rejected for
-//            drifting at large N_f) is re-seeded from the exact phase every F
-//            steps, which bounds the drift by ~F ulp.
+// sin/cos, three modes (ls_device.cuh, Strip::add):
+//   MUFU   -- every (j, k) takes the hardware sin/cos of the phase (the
+//             paper's __sincosf, Sec. 4.3), stepping the 32-bit phase by
+//             round(u / 2^32): 2 SFU ops per term.
+//   RECUR  -- the hardware sin/cos seeds the first k of the strip; the next
+//             F-1 follow from the angle-addition formulas with the per-sample
+//             rotation (cos, sin)(2 pi u_j): 4 FMA-pipe ops per term.  The
+//             recurrence (the trig recursion of Sec. 3, there rejected for
+//             drifting at large N_f) is re-seeded from the exact phase every F
+//             steps, which bounds the drift by ~F ulp.
+//   RECUR3 -- one angle-addition step, then the three-term form of the same
+//             identity, z_{k+1} = 2 cos(2 pi u_j) z_k - z_{k-1}: 2 FMA-pipe ops
+//             per term.  Its rounding error grows like F^2 ulp, and like
+//             F ulp / sin(2 pi u_j) for samples whose step angle is near 0 or pi.
 // NAIVE_FP32 -- the paper's own single-precision phase f*t - rintf(f*t)
-//            (Sec. 4.3), kept as a comparator.
-#include <cstdio>
-
-#include "lsp_kernels.cuh"
+//             (Sec. 4.3), kept as a comparator.
+#include "ls_device.cuh"
 
 namespace lsp {
 namespace {
 
-constexpr float kTwoPi = 6.28318530717958647692f;
-constexpr float kThreePi = 9.42477796076937971538f;
-
-// Top 23 bits of a 32-bit turn fraction, offset by half a turn at prep time,
-// become a float in [1, 2) by pasting them under the exponent of 1.0; one FMA
-// maps that to an angle in [-pi, pi).  No int->float conversion unit is used.
-__device__ __forceinline__ float phase_to_angle(uint32_t p) {
-    return fmaf(__uint_as_float(0x3F800000u | (p >> 9)), kTwoPi, -kThreePi);
-}
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Eq. 5 with tau from Eq. 6, in closed form.  With A = CC - SS = 2CC - N,
-// B = 2CS and R = |A + iB| = |sum exp(2 i w t_j)|, tan 2wtau = B/A gives
-// cos 2wtau = A/R, sin 2wtau = B/R, and the two denominators of Eq. 5 are
-// (N + R)/2 and (N - R)/2; the two numerators are (|Z|^2 +- Re(e^{-2iwtau} Z^2))/2
-// with Z = XC + i XS.  No trig, and R = 0 (tau undefined) takes wtau = 0.
-// A term whose denominator is below N 2^-16 is taken as zero.
-__device__ __forceinline__ float periodogram_value(float XC, float XS, float CC, float CS, float n) {
-    const float A = 2.f * CC - n;
-    const float B = 2.f * CS;
-    const float R = sqrtf(A * A + B * B);
-    float c2 = 1.f, s2 = 0.f;
-    if (R > 0.f) {
-        c2 = A / R;
-        s2 = B / R;
-    }
-    const float z2 = XC * XC + XS * XS;
-    const float cross = c2 * (XC * XC - XS * XS) + s2 * (2.f * XC * XS);
-    const float num1 = fmaxf(0.5f * (z2 + cross), 0.f);
-    const float num2 = fmaxf(0.5f * (z2 - cross), 0.f);
-    const float den1 = 0.5f * (n + R);
-    const float den2 = 0.5f * (n - R);
-    const float thr = n * (1.f / 65536.f);
-    float P = 0.f;
-    if (den1 > thr) P += num1 / den1;
-    if (den2 > thr) P += num2 / den2;
-    return 0.5f * P;
-}
+using namespace dev;
 
 template <int F>
 __device__ __forceinline__ void write_out(const float (&xc)[F], const float (&xs)[F], const float (&cc)[F],
@@ -111,85 +66,21 @@ template <int F, int MODE>
 __global__ void __launch_bounds__(kMainThreads)
 ls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, int64_t N, int64_t chunk,
                int N_f, int64_t nf_pad, float* __restrict__ part, float* __restrict__ P_out) {
-    __shared__ __align__(16) uint4 sA[2][kTile];
-    __shared__ __align__(16) float4 sB[2][kTile];
-    const int tid = threadIdx.x;
-    const uint32_t k0 = (uint32_t)blockIdx.x * (kMainThreads * F) + (uint32_t)tid * F;
+    __shared__ __align__(16) TileSmem<false> sm;
+    const uint32_t k0 = (uint32_t)blockIdx.x * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
     const int64_t j0 = (int64_t)blockIdx.y * chunk;
     const int64_t j1 = min(N, j0 + chunk);
-    const int ntiles = j1 > j0 ? (int)((j1 - j0 + kTile - 1) / kTile) : 0;
-
-    float xc[F], xs[F], cc[F], cs[F];
-#pragma unroll
-    for (int i = 0; i < F; ++i) xc[i] = xs[i] = cc[i] = cs[i] = 0.f;
-
-    if (ntiles > 0) {
-        const int n = (int)min((int64_t)kTile, j1 - j0);
-        for (int q = tid; q < n; q += kMainThreads) {
-            cp_async16(&sA[0][q], recA + j0 + q);
-            cp_async16(&sB[0][q], recB + j0 + q);
-        }
-    }
-    cp_async_commit();
-
-    for (int it = 0; it < ntiles; ++it) {
-        const int64_t jt = j0 + (int64_t)it * kTile;
-        if (it + 1 < ntiles) {
-            const int64_t jn = jt + kTile;
-            const int n = (int)min((int64_t)kTile, j1 - jn);
-            const int buf = (it + 1) & 1;
-            for (int q = tid; q < n; q += kMainThreads) {
-                cp_async16(&sA[buf][q], recA + jn + q);
-                cp_async16(&sB[buf][q], recB + jn + q);
-            }
-        }
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const int n = (int)min((int64_t)kTile, j1 - jt);
-        const uint4* a = sA[it & 1];
-        const float4* bb = sB[it & 1];
+    Strip<F, MODE> st;
+    st.zero();
+    for_each_tile<false>(sm, recA, recB, nullptr, j0, j1,
+                         [&](const uint4* a, const float4* b, const float*, int n) {
 #pragma unroll 2
-        for (int j = 0; j < n; ++j) {
-            const uint4 A = a[j];
-            const float4 B = bb[j];
-            const uint64_t u = ((uint64_t)A.y << 32) | A.x;
-            const uint64_t v = ((uint64_t)A.w << 32) | A.z;
-            uint32_t p = (uint32_t)((v + (uint64_t)k0 * u) >> 32);
-            const float x = B.x;
-            if (MODE == 1) {
-                const uint32_t du = __float_as_uint(B.w);
-#pragma unroll
-                for (int i = 0; i < F; ++i) {
-                    float s, c;
-                    __sincosf(phase_to_angle(p), &s, &c);
-                    xc[i] = fmaf(x, c, xc[i]);
-                    xs[i] = fmaf(x, s, xs[i]);
-                    cc[i] = fmaf(c, c, cc[i]);
-                    cs[i] = fmaf(c, s, cs[i]);
-                    p += du;
-                }
-            } else {
-                const float C = B.y, S = B.z;
-                float s, c;
-                __sincosf(phase_to_angle(p), &s, &c);
-#pragma unroll
-                for (int i = 0; i < F; ++i) {
-                    xc[i] = fmaf(x, c, xc[i]);
-                    xs[i] = fmaf(x, s, xs[i]);
-                    cc[i] = fmaf(c, c, cc[i]);
-                    cs[i] = fmaf(c, s, cs[i]);
-                    if (i + 1 < F) {
-                        const float cn = fmaf(c, C, -s * S);
-                        s = fmaf(s, C, c * S);
-                        c = cn;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    write_out<F>(xc, xs, cc, cs, k0, N_f, nf_pad, N, part, P_out);
+                             for (int j = 0; j < n; ++j) {
+                                 const float4 B = b[j];
+                                 st.add(a[j], B, B.x, k0);
+                             }
+                         });
+    write_out<F>(st.xc, st.xs, st.cc, st.cs, k0, N_f, nf_pad, N, part, P_out);
 }
 
 // The paper's single-precision phase (Sec. 4.3): f_k = (float)(f0 + k df),
@@ -274,31 +165,41 @@ finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, int N
 using MainFn = void (*)(const uint4*, const float4*, int64_t, int64_t, int, int64_t, float*, float*);
 using NaiveFn = void (*)(const float2*, int64_t, int64_t, int, int64_t, double, double, float*, float*);
 
-MainFn main_fn(int mode, int F) {
-    if (mode == 1) {
-        if (F == 4) return ls_main_kernel<4, 1>;
-        if (F == 8) return ls_main_kernel<8, 1>;
-        if (F == 16) return ls_main_kernel<16, 1>;
-    } else if (mode == 2) {
-        if (F == 4) return ls_main_kernel<4, 2>;
-        if (F == 8) return ls_main_kernel<8, 2>;
-        if (F == 16) return ls_main_kernel<16, 2>;
+template <int MODE>
+MainFn main_fn_f(int F) {
+    switch (F) {
+        case 4: return ls_main_kernel<4, MODE>;
+        case 8: return ls_main_kernel<8, MODE>;
+        case 16: return ls_main_kernel<16, MODE>;
+        case 24: return ls_main_kernel<24, MODE>;
+        default: return nullptr;
     }
-    return nullptr;
+}
+
+MainFn main_fn(int mode, int F) {
+    switch (mode) {
+        case kMufu: return main_fn_f<kMufu>(F);
+        case kRecur: return main_fn_f<kRecur>(F);
+        case kRecur3: return main_fn_f<kRecur3>(F);
+        default: return nullptr;
+    }
 }
 
 NaiveFn naive_fn(int F) {
-    if (F == 4) return ls_naive_kernel<4>;
-    if (F == 8) return ls_naive_kernel<8>;
-    if (F == 16) return ls_naive_kernel<16>;
-    return nullptr;
+    switch (F) {
+        case 4: return ls_naive_kernel<4>;
+        case 8: return ls_naive_kernel<8>;
+        case 16: return ls_naive_kernel<16>;
+        case 24: return ls_naive_kernel<24>;
+        default: return nullptr;
+    }
 }
 
 }  // namespace
 
 int main_occupancy(int mode, int F) {
     int nb = 0;
-    const void* fn = mode == 3 ? (const void*)naive_fn(F) : (const void*)main_fn(mode, F);
+    const void* fn = mode == dev::kNaive ? (const void*)naive_fn(F) : (const void*)main_fn(mode, F);
     if (!fn) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kMainThreads, 0) != cudaSuccess) {
         cudaGetLastError();
@@ -312,7 +213,7 @@ cudaError_t launch_main(const MainShape& s, const uint4* recA, const float4* rec
                         cudaStream_t st) {
     dim3 grid((unsigned)s.nfb, (unsigned)s.split);
     float* direct = s.split == 1 ? P_out : nullptr;
-    if (s.mode == 3) {
+    if (s.mode == dev::kNaive) {
         NaiveFn fn = naive_fn(s.F);
         if (!fn) return cudaErrorInvalidValue;
         fn<<<grid, kMainThreads, 0, st>>>(recN, N, s.chunk, (int)N_f, s.nf_pad, f0, df, part, direct);

@@ -9,135 +9,51 @@
 #include <string>
 #include <thread>
 
-#include "lsp.h"
-#include "lsp_kernels.cuh"
+#include "lsp_ctx.h"
 
 using lsp::CurveStats;
 using lsp::MainShape;
+using namespace lsp::host;
 
 namespace {
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-};
-
-}  // namespace
-
-struct lsp_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;
-    lsp_options opt{};
-    std::string err;
-    int sms = 0;
-    // workspace
-    DevBuf recA, recB, recN, part, stats, t_stage, x_stage, p_stage;
-    int* status_d = nullptr;  // device status word (OR of kStatus* bits)
-    int* status_h = nullptr;  // pinned mirror
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t done = nullptr;
-    bool timing_valid = false;
-    bool has_finalize = false;
-    int last_launches = 0;
-};
-
-namespace {
-
-// Makes the context's device current for the scope of a call and restores the
-// caller's device afterwards.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            cudaGetLastError();
-            prev = -1;
-        }
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-lsp_status fail(lsp_ctx* ctx, lsp_status st, const char* fmt, ...) {
-    if (ctx) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        ctx->err = buf;
-    }
-    return st;
-}
-
-lsp_status cuda_fail(lsp_ctx* ctx, cudaError_t e, const char* what) {
-    return fail(ctx, e == cudaErrorMemoryAllocation ? LSP_ERR_OOM : LSP_ERR_CUDA, "%s: %s", what,
-                cudaGetErrorString(e));
-}
-
-#define LSP_CUDA(ctx, call)                                   \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-    } while (0)
-
-// Grow a workspace buffer to at least `bytes` (contents are not kept).
-lsp_status ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
-    if (bytes <= b.cap) return LSP_OK;
-    if (b.p) {
-        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        LSP_CUDA(ctx, cudaFree(b.p));
-        b.p = nullptr;
-        b.cap = 0;
-    }
-    size_t want = bytes + bytes / 4 + 256;
-    cudaError_t e = cudaMalloc(&b.p, want);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        b.p = nullptr;
-        return cuda_fail(ctx, e, "cudaMalloc(workspace)");
-    }
-    b.cap = want;
-    return LSP_OK;
-}
-
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
-    if (o->sincos_mode < 0 || o->sincos_mode > 2)
+    if (o->sincos_mode < 0 || o->sincos_mode > 3)
         return fail(ctx, LSP_ERR_INVALID_ARG, "sincos_mode %d out of range", o->sincos_mode);
     if (o->phase_mode < 0 || o->phase_mode > 1)
         return fail(ctx, LSP_ERR_INVALID_ARG, "phase_mode %d out of range", o->phase_mode);
     if (o->freqs_per_thread != 0 && o->freqs_per_thread != 4 && o->freqs_per_thread != 8 &&
-        o->freqs_per_thread != 16)
-        return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8 or 16");
+        o->freqs_per_thread != 16 && o->freqs_per_thread != 24)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8, 16 or 24");
     if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");
     for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "reserved option fields must be zero");
     return LSP_OK;
 }
 
+}  // namespace
+
 // Launch shape: mode, strip length F, N_t split.  The split is chosen so the
 // grid fills whole waves of resident CTAs while every chunk keeps at least
 // one tile of samples.
-MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
+MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
     const lsp_options& o = ctx->opt;
-    if (o.phase_mode == LSP_PHASE_NAIVE_FP32)
-        s.mode = 3;
-    else
-        s.mode = o.sincos_mode == LSP_SINCOS_MUFU ? 1 : 2;
-    s.F = o.freqs_per_thread ? o.freqs_per_thread : (s.mode == 2 ? 16 : 8);
+    // Strip lengths measured best on GB300 for each mode (gapped_100k workload).
+    if (o.phase_mode == LSP_PHASE_NAIVE_FP32) {
+        s.mode = lsp::kModeNaive;
+        s.F = 8;
+    } else if (o.sincos_mode == LSP_SINCOS_MUFU) {
+        s.mode = lsp::kModeMufu;
+        s.F = 8;
+    } else if (o.sincos_mode == LSP_SINCOS_RECUR) {
+        s.mode = lsp::kModeRecur;
+        s.F = 16;
+    } else {
+        s.mode = lsp::kModeRecur3;
+        s.F = 24;
+    }
+    if (o.freqs_per_thread) s.F = o.freqs_per_thread;
     const int64_t per_block = lsp::freqs_per_block(s.F);
     s.nfb = (int)((N_f + per_block - 1) / per_block);
     s.nf_pad = (int64_t)s.nfb * per_block;
@@ -165,8 +81,6 @@ MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     s.split = (int)((N + s.chunk - 1) / s.chunk);
     return s;
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -265,7 +179,10 @@ lsp_status lsp_periodogram(lsp_ctx* ctx, const double* t, const double* X, int64
     if ((rs = ensure(ctx, ctx->recA, (size_t)N_t * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->recB, (size_t)N_t * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->stats, sizeof(CurveStats))) != LSP_OK) return rs;
-    if (s.mode == 3 && (rs = ensure(ctx, ctx->recN, (size_t)N_t * 8)) != LSP_OK) return rs;
+    const int slices = lsp::prep_stats_slices(1, N_t);
+    if ((rs = ensure(ctx, ctx->stat_parts, sizeof(lsp::StatPart) * (size_t)slices)) != LSP_OK) return rs;
+    if ((rs = ensure_zeroed(ctx, ctx->stat_counters, sizeof(unsigned))) != LSP_OK) return rs;
+    if (s.mode == lsp::kModeNaive && (rs = ensure(ctx, ctx->recN, (size_t)N_t * 8)) != LSP_OK) return rs;
     if (s.split > 1 && (rs = ensure(ctx, ctx->part, (size_t)s.split * 4 * (size_t)s.nf_pad * 4)) != LSP_OK)
         return rs;
     if (!t_dev && (rs = ensure(ctx, ctx->t_stage, (size_t)N_t * 8)) != LSP_OK) return rs;
@@ -286,10 +203,11 @@ lsp_status lsp_periodogram(lsp_ctx* ctx, const double* t, const double* X, int64
     const bool timing = ctx->opt.timing != 0;
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     CurveStats* stats = (CurveStats*)ctx->stats.p;
-    LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d, st));
+    LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d,
+                                         (lsp::StatPart*)ctx->stat_parts.p, (unsigned*)ctx->stat_counters.p, st));
     LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
                                            (uint4*)ctx->recA.p, (float4*)ctx->recB.p,
-                                           s.mode == 3 ? (float2*)ctx->recN.p : nullptr, st));
+                                           s.mode == lsp::kModeNaive ? (float2*)ctx->recN.p : nullptr, nullptr, st));
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     LSP_CUDA(ctx, lsp::launch_main(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
                                    (const float2*)ctx->recN.p, N_t, N_f, f_0, df, (float*)ctx->part.p, pd, st));
@@ -359,12 +277,17 @@ void lsp_destroy(lsp_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    DevBuf* bufs[] = {&ctx->recA, &ctx->recB, &ctx->recN, &ctx->part, &ctx->stats,
-                      &ctx->t_stage, &ctx->x_stage, &ctx->p_stage};
+    drop_plan(ctx);
+    DevBuf* bufs[] = {&ctx->recA,   &ctx->recB,   &ctx->recN,   &ctx->part,    &ctx->stats,  &ctx->t_stage,
+                      &ctx->x_stage, &ctx->p_stage, &ctx->stat_parts, &ctx->stat_counters, &ctx->b_recA,
+                      &ctx->b_recB,  &ctx->b_xr,   &ctx->b_stats, &ctx->b_items, &ctx->b_head, &ctx->b_maxkey,
+                      &ctx->b_seed,  &ctx->b_off,  &ctx->b_nf,   &ctx->b_f0,    &ctx->b_df,   &ctx->b_poff,
+                      &ctx->b_t,     &ctx->b_X,    &ctx->b_P,    &ctx->b_maxP,  &ctx->b_argmax};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     if (ctx->status_d) cudaFree(ctx->status_d);
     if (ctx->status_h) cudaFreeHost(ctx->status_h);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->done) cudaEventDestroy(ctx->done);

@@ -1,0 +1,302 @@
+// lsp_batch_api.cu -- lsp_batch and lsp_noise of include/lsp.h.
+//
+// lsp_batch plans a batch on the host (metadata checks, the work list sorted
+// longest curve first) and runs it as one CUDA graph: statistics and phase
+// records of every curve, the noise of every realization (when X is NULL),
+// the persistent periodogram kernel and the unpacking of the per-curve
+// maxima.  The graph is cached with the plan and replayed as long as the
+// pointers and the metadata of later calls are the same; a new seed is
+// written to device memory before the launch, so it does not need a new graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "lsp_ctx.h"
+
+using namespace lsp::host;
+using lsp::MainShape;
+
+void lsp::host::drop_plan(lsp_ctx* ctx) {
+    if (ctx->plan.exec) cudaGraphExecDestroy(ctx->plan.exec);
+    ctx->plan = BatchPlan();
+}
+
+namespace {
+
+// Copy n elements of a host or device array into a host vector (ordered on
+// the context's stream, then waited for).
+template <class T>
+lsp_status fetch(lsp_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
+    dst.resize(n);
+    if (n == 0) return LSP_OK;
+    if (is_device_ptr(src)) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::memcpy(dst.data(), src, n * sizeof(T));
+    }
+    return LSP_OK;
+}
+
+lsp_status ensure_pinned(lsp_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->pinned_cap) return LSP_OK;
+    if (ctx->pinned) {
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_cap = 0;
+    }
+    const size_t want = bytes + bytes / 4 + 4096;
+    LSP_CUDA(ctx, cudaMallocHost(&ctx->pinned, want));
+    ctx->pinned_cap = want;
+    return LSP_OK;
+}
+
+// Device view of a caller array: the array itself if it is on the device,
+// else a context buffer filled from it (asynchronously, outside the graph).
+template <class T>
+lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf, const T** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return LSP_OK;
+    }
+    lsp_status st = ensure(ctx, buf, n * sizeof(T) + 16);
+    if (st != LSP_OK) return st;
+    if (n) LSP_CUDA(ctx, cudaMemcpyAsync(buf.p, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    *out = (const T*)buf.p;
+    return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                     uint64_t seed, int32_t n_real, const double* f_0, const double* df, const int64_t* N_f,
+                     float* P_out, const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->timing_valid = false;
+    ctx->last_launches = 0;
+    if (n_curves < 1 || n_curves > 65535)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "n_curves = %d out of range [1, 65535]", n_curves);
+    if (n_real < 1 || n_real > 65535) return fail(ctx, LSP_ERR_INVALID_ARG, "n_real = %d out of range", n_real);
+    if (X && n_real != 1) return fail(ctx, LSP_ERR_INVALID_ARG, "with measured X, n_real must be 1");
+    if (!t_off || !t || !f_0 || !df || !N_f) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
+    if (!P_out && !maxP_out && !argmax_out) return fail(ctx, LSP_ERR_INVALID_ARG, "no output requested");
+    if (P_out && !P_off) return fail(ctx, LSP_ERR_INVALID_ARG, "P_out needs P_off");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    lsp_status rs;
+
+    // ---- metadata on the host, checked ----
+    std::vector<int64_t> off, nf, poff;
+    std::vector<double> f0v, dfv;
+    if ((rs = fetch(ctx, t_off, (size_t)n_curves + 1, off)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, N_f, (size_t)n_curves, nf)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, f_0, (size_t)n_curves, f0v)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, df, (size_t)n_curves, dfv)) != LSP_OK) return rs;
+    if (P_out && (rs = fetch(ctx, P_off, (size_t)n_curves + 1, poff)) != LSP_OK) return rs;
+    if (off[0] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "t_off[0] must be 0");
+    for (int c = 0; c < n_curves; ++c) {
+        if (off[c + 1] - off[c] < 2)
+            return fail(ctx, LSP_ERR_INVALID_ARG, "curve %d has %lld samples (need >= 2)", c,
+                        (long long)(off[c + 1] - off[c]));
+        if (nf[c] < 0 || nf[c] >= (int64_t(1) << 31))
+            return fail(ctx, LSP_ERR_INVALID_ARG, "N_f[%d] = %lld out of range", c, (long long)nf[c]);
+        if (!std::isfinite(f0v[c]) || !std::isfinite(dfv[c]))
+            return fail(ctx, LSP_ERR_NONFINITE, "grid of curve %d is not finite", c);
+        if (P_out && (poff[c + 1] - poff[c] < nf[c] || poff[c] < 0))
+            return fail(ctx, LSP_ERR_INVALID_ARG, "P_off leaves fewer than N_f[%d] slots", c);
+    }
+    const int64_t total = off[n_curves];
+    const int64_t P_total = P_out ? poff[n_curves] : 0;
+    const bool noise = X == nullptr;
+
+    // ---- launch shape: the single-curve choice of mode and strip length ----
+    const MainShape shape = choose_shape(ctx, 2 * lsp::kTile, 1);
+    if (shape.mode == lsp::kModeNaive)
+        return fail(ctx, LSP_ERR_UNSUPPORTED, "lsp_batch does not offer the naive FP32 phase");
+    const int mode = shape.mode, F = shape.F;
+    const int64_t per_block = lsp::freqs_per_block(F);
+
+    // ---- device views of the inputs (host arrays are copied in, outside the graph) ----
+    const int64_t *d_off = nullptr, *d_nf = nullptr, *d_poff = nullptr;
+    const double *d_f0 = nullptr, *d_df = nullptr, *d_t = nullptr, *d_X = nullptr;
+    if ((rs = device_view(ctx, t_off, (size_t)n_curves + 1, ctx->b_off, &d_off)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, N_f, (size_t)n_curves, ctx->b_nf, &d_nf)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, f_0, (size_t)n_curves, ctx->b_f0, &d_f0)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, df, (size_t)n_curves, ctx->b_df, &d_df)) != LSP_OK) return rs;
+    if (P_out && (rs = device_view(ctx, P_off, (size_t)n_curves + 1, ctx->b_poff, &d_poff)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, t, (size_t)total, ctx->b_t, &d_t)) != LSP_OK) return rs;
+    if (!noise && (rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
+    const bool p_dev = !P_out || is_device_ptr(P_out);
+    const bool m_dev = !maxP_out || is_device_ptr(maxP_out);
+    const bool a_dev = !argmax_out || is_device_ptr(argmax_out);
+    const size_t n_out = (size_t)n_real * (size_t)n_curves;
+
+    // ---- workspace (all allocations happen before any capture) ----
+    if ((rs = ensure(ctx, ctx->b_recA, (size_t)total * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_recB, (size_t)total * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_xr, (size_t)n_real * (size_t)total * 4)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_stats, sizeof(lsp::CurveStats) * (size_t)n_curves)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_head, 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_seed, 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_maxkey, n_out * 8)) != LSP_OK) return rs;
+    if (!p_dev && (rs = ensure(ctx, ctx->b_P, (size_t)n_real * (size_t)P_total * 4)) != LSP_OK) return rs;
+    if (!m_dev && (rs = ensure(ctx, ctx->b_maxP, n_out * 4)) != LSP_OK) return rs;
+    if (!a_dev && (rs = ensure(ctx, ctx->b_argmax, n_out * 4)) != LSP_OK) return rs;
+    float* d_P = P_out ? (p_dev ? P_out : (float*)ctx->b_P.p) : nullptr;
+    float* d_maxP = maxP_out ? (m_dev ? maxP_out : (float*)ctx->b_maxP.p) : nullptr;
+    int32_t* d_argmax = argmax_out ? (a_dev ? argmax_out : (int32_t*)ctx->b_argmax.p) : nullptr;
+
+    // ---- plan: reuse the cached graph when nothing it depends on changed ----
+    const std::vector<const void*> ptrs = {d_off, d_nf, d_f0, d_df, d_poff, d_t, d_X, d_P, d_maxP, d_argmax,
+                                           ctx->b_recA.p, ctx->b_recB.p, ctx->b_xr.p, ctx->b_stats.p,
+                                           ctx->b_head.p, ctx->b_seed.p, ctx->b_maxkey.p, ctx->b_items.p};
+    BatchPlan& pl = ctx->plan;
+    const bool same = pl.valid && pl.n_curves == n_curves && pl.n_real == n_real && pl.mode == mode &&
+                      pl.F == F && pl.noise == noise && pl.ptrs == ptrs && pl.t_off == off && pl.nf == nf &&
+                      pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
+    if (!same) {
+        drop_plan(ctx);
+        // work list: curves longest first (each item costs ~N_t), then blocks, then realizations
+        std::vector<int> order(n_curves);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+        std::vector<lsp::BatchItem> items;
+        for (int c : order) {
+            const int64_t nfb = (nf[c] + per_block - 1) / per_block;
+            for (int64_t fb = 0; fb < nfb; ++fb)
+                for (int r = 0; r < n_real; ++r) items.push_back({c, r, (int32_t)fb, 0});
+        }
+        if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
+        const size_t item_bytes = items.size() * sizeof(lsp::BatchItem);
+        const void* old_items = ctx->b_items.p;
+        if ((rs = ensure(ctx, ctx->b_items, item_bytes + 16)) != LSP_OK) return rs;
+        if ((rs = ensure_pinned(ctx, item_bytes + 64)) != LSP_OK) return rs;
+        LSP_CUDA(ctx, cudaStreamSynchronize(st));  // the pinned buffer may still feed an earlier copy
+        if (!items.empty()) {
+            std::memcpy(ctx->pinned, items.data(), item_bytes);
+            LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_items.p, ctx->pinned, item_bytes, cudaMemcpyHostToDevice, st));
+        }
+        std::vector<const void*> ptrs2 = ptrs;
+        ptrs2.back() = ctx->b_items.p;
+        (void)old_items;
+        const int occ = lsp::batch_occupancy(mode, F);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
+
+        // capture the batch as one graph
+        cudaGraph_t g = nullptr;
+        LSP_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(ctx->b_head.p, 0, 16, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_maxkey.p, 0, n_out * 8, st);
+        if (e == cudaSuccess)
+            e = lsp::launch_prep_stats(d_t, d_X, d_off, 0, n_curves, (lsp::CurveStats*)ctx->b_stats.p,
+                                       ctx->status_d, nullptr, nullptr, st);
+        if (e == cudaSuccess) {
+            const int64_t max_n = off[order[0] + 1] - off[order[0]];
+            e = lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0,
+                                         (const lsp::CurveStats*)ctx->b_stats.p, (uint4*)ctx->b_recA.p,
+                                         (float4*)ctx->b_recB.p, nullptr, noise ? nullptr : (float*)ctx->b_xr.p,
+                                         st);
+        }
+        if (e == cudaSuccess && noise)
+            e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
+                                       (float*)ctx->b_xr.p, st);
+        if (e == cudaSuccess && !items.empty())
+            e = lsp::launch_batch(mode, F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+                                  (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves,
+                                  (const uint4*)ctx->b_recA.p, (const float4*)ctx->b_recB.p,
+                                  (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
+                                  (unsigned long long*)ctx->b_maxkey.p, st);
+        if (e == cudaSuccess && (d_maxP || d_argmax))
+            e = lsp::launch_unpack_max((const unsigned long long*)ctx->b_maxkey.p, (int64_t)n_out, d_maxP,
+                                       d_argmax, st);
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            drop_plan(ctx);
+            return cuda_fail(ctx, e, "capturing the batch graph");
+        }
+        pl.valid = true;
+        pl.ptrs = ptrs2;
+        pl.n_curves = n_curves;
+        pl.n_real = n_real;
+        pl.mode = mode;
+        pl.F = F;
+        pl.noise = noise;
+        pl.t_off = off;
+        pl.nf = nf;
+        pl.f0 = f0v;
+        pl.df = dfv;
+        pl.p_off = poff;
+        pl.n_items = (int)items.size();
+        pl.grid = grid;
+        pl.kernels = 3 + (noise ? 1 : 0) + ((d_maxP || d_argmax) ? 1 : 0) + (items.empty() ? -1 : 0);
+    }
+
+    // ---- run: new seed, one graph launch, outputs back if they live on the host ----
+    if ((rs = ensure_pinned(ctx, 64)) != LSP_OK) return rs;
+    LSP_CUDA(ctx, cudaStreamSynchronize(st));  // the pinned seed slot may still feed an earlier copy
+    std::memcpy(ctx->pinned, &seed, sizeof seed);
+    LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_seed.p, ctx->pinned, sizeof seed, cudaMemcpyHostToDevice, st));
+    const bool timing = ctx->opt.timing != 0;
+    if (timing) {
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+    }
+    LSP_CUDA(ctx, cudaGraphLaunch(pl.exec, st));
+    if (timing) {
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
+        ctx->timing_valid = true;
+        ctx->has_finalize = false;
+    }
+    ctx->last_launches = pl.kernels;
+    bool host_out = false;
+    if (P_out && !p_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(P_out, d_P, (size_t)n_real * (size_t)P_total * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (maxP_out && !m_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(maxP_out, d_maxP, n_out * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (argmax_out && !a_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(argmax_out, d_argmax, n_out * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) return lsp_sync(ctx, -1.0);
+    return LSP_OK;
+}
+
+lsp_status lsp_noise(lsp_ctx* ctx, uint64_t seed, int32_t curve, int32_t real, int64_t N, float* out) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (N < 0 || curve < 0 || real < 0 || (N > 0 && !out)) return fail(ctx, LSP_ERR_INVALID_ARG, "bad argument");
+    if (N == 0) return LSP_OK;
+    if (N > (int64_t(1) << 34)) return fail(ctx, LSP_ERR_INVALID_ARG, "N too large");
+    DeviceGuard guard(ctx->device);
+    const bool dev = is_device_ptr(out);
+    float* d = out;
+    if (!dev) {
+        lsp_status rs = ensure(ctx, ctx->p_stage, (size_t)N * 4);
+        if (rs != LSP_OK) return rs;
+        d = (float*)ctx->p_stage.p;
+    }
+    LSP_CUDA(ctx, lsp::launch_noise_raw(seed, (uint32_t)curve, (uint32_t)real, N, d, ctx->stream));
+    ctx->last_launches = 1;
+    if (!dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(out, d, (size_t)N * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        return lsp_sync(ctx, -1.0);
+    }
+    return LSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// lsp_ctx.h -- the context structure and host-side helpers shared by the
+// C-ABI implementation files (lsp_api.cu, lsp_batch_api.cu).  Internal.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "lsp.h"
+#include "lsp_kernels.cuh"
+
+namespace lsp {
+namespace host {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Cached plan of the last lsp_batch call: the host copy of its metadata, the
+// sorted work list and the instantiated CUDA graph that replays the whole
+// batch (prep, noise, persistent kernel, max unpack) in one launch.
+struct BatchPlan {
+    bool valid = false;
+    std::vector<const void*> ptrs;          // every pointer argument of the call
+    int n_curves = 0, n_real = 0, mode = 0, F = 0;
+    bool noise = false;
+    std::vector<int64_t> t_off, nf, p_off;
+    std::vector<double> f0, df;
+    int n_items = 0, grid = 0;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+};
+
+}  // namespace host
+}  // namespace lsp
+
+struct lsp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    lsp_options opt{};
+    std::string err;
+    int sms = 0;
+    // single-curve workspace
+    lsp::host::DevBuf recA, recB, recN, part, stats, t_stage, x_stage, p_stage, stat_parts, stat_counters;
+    // batch workspace
+    lsp::host::DevBuf b_recA, b_recB, b_xr, b_stats, b_items, b_head, b_maxkey, b_seed, b_off, b_nf, b_f0,
+        b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax;
+    void* pinned = nullptr;  // host staging for the work list and small values
+    size_t pinned_cap = 0;
+    lsp::host::BatchPlan plan;
+    int* status_d = nullptr;  // device status word (OR of kStatus* bits)
+    int* status_h = nullptr;  // pinned mirror
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t done = nullptr;
+    bool timing_valid = false;
+    bool has_finalize = false;
+    int last_launches = 0;
+};
+
+namespace lsp {
+namespace host {
+
+// Makes the context's device current for the scope of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+inline lsp_status fail(lsp_ctx* ctx, lsp_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+inline lsp_status cuda_fail(lsp_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? LSP_ERR_OOM : LSP_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LSP_CUDA(ctx, call)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return lsp::host::cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Grow a workspace buffer to at least `bytes` (contents are not kept).
+inline lsp_status ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap) return LSP_OK;
+    if (b.p) {
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        LSP_CUDA(ctx, cudaFree(b.p));
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return cuda_fail(ctx, e, "cudaMalloc(workspace)");
+    }
+    b.cap = want;
+    return LSP_OK;
+}
+
+// As ensure(), but a newly allocated buffer is zero-filled (for counters
+// that kernels leave at zero after use).
+inline lsp_status ensure_zeroed(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes <= b.cap) return LSP_OK;
+    lsp_status st = ensure(ctx, b, bytes);
+    if (st != LSP_OK) return st;
+    LSP_CUDA(ctx, cudaMemsetAsync(b.p, 0, b.cap, ctx->stream));
+    return LSP_OK;
+}
+
+inline bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Launch shape of the single-curve path for the context's options.
+lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
+
+// Release the cached batch graph.
+void drop_plan(lsp_ctx* ctx);
+
+}  // namespace host
+}  // namespace lsp

@@ -30,19 +30,38 @@ struct CurveStats {
 // the 23-bit mantissa taken from the top word).
 constexpr uint64_t kPhaseOffset = (1ull << 63) + (1ull << 40) + (1ull << 31);
 
+// Per-slice partial statistics when several CTAs share one curve.
+struct StatPart {
+    double n, mean, m2, tmin;
+    int bad, pad;
+};
+
+// At most this many CTAs compute the statistics of one curve.
+constexpr int kMaxStatSlices = 128;
+
+// CTAs per curve that launch_prep_stats will use (parts needs n_curves * that
+// entries; counters needs n_curves zero-initialized words, left zero after use).
+int prep_stats_slices(int n_curves, int64_t n0);
+
 // Kernel launchers (all asynchronous on `st`).
 // Curves are given in CSR form: samples of curve c are [off[c], off[c+1]).
 // When off == nullptr there is one curve of n0 samples.
 cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
-                              int n_curves, CurveStats* stats, int* status, cudaStream_t st);
+                              int n_curves, CurveStats* stats, int* status, StatPart* parts,
+                              unsigned* counters, cudaStream_t st);
 
+// X may be null (noise batches): then only t_ref is computed and x_hat = 0.
+// xout, if given, receives x_hat as a plain FP32 array (batch layout).
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
-                                uint4* recA, float4* recB, float2* recN, cudaStream_t st);
+                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st);
+
+// Kernel modes (how sin/cos and the phase are formed in the O(N_t N_f) loop).
+enum : int { kModeMufu = 1, kModeRecur = 2, kModeNaive = 3, kModeRecur3 = 4 };
 
 struct MainShape {
-    int mode;      // 1 = MUFU, 2 = RECUR, 3 = NAIVE_FP32
+    int mode;      // kMode*
     int F;         // adjacent frequencies per thread
     int split;     // N_t chunks per frequency block
     int64_t chunk; // samples per chunk
@@ -65,5 +84,35 @@ cudaError_t launch_main(const MainShape& s, const uint4* recA, const float4* rec
 
 cudaError_t launch_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f,
                             float* P_out, cudaStream_t st);
+
+// ---- batched evaluation (batch.cu) and noise (noise.cu) ----
+
+// One work item of the persistent batch kernel: a block of kMainThreads*F
+// frequencies of one realization of one curve.
+struct BatchItem {
+    int32_t curve;
+    int32_t real;
+    int32_t fblock;
+    int32_t pad;
+};
+
+int batch_occupancy(int mode, int F);
+
+cudaError_t launch_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+                         const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,
+                         const float4* recB, const float* xr, float* P_out, const int64_t* P_off, int64_t P_total,
+                         unsigned long long* maxkey, cudaStream_t st);
+
+cudaError_t launch_unpack_max(const unsigned long long* maxkey, int64_t n, float* maxP, int32_t* argmax,
+                              cudaStream_t st);
+
+// Raw N(0,1) values of (seed, curve, realization), samples 0..n-1.
+cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float* out, cudaStream_t st);
+
+// Normalized noise for every (curve, realization) into xr[real][total]; the
+// seed is read from device memory so a captured graph can be replayed with
+// a new seed.
+cudaError_t launch_noise_prep(const int64_t* off, int n_curves, int n_real, const uint64_t* seed_dev,
+                              int64_t total, float* xr, cudaStream_t st);
 
 }  // namespace lsp

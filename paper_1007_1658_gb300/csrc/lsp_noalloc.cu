@@ -17,11 +17,11 @@
 
 namespace {
 
-constexpr size_t kHeaderBytes = 256;                   // CurveStats + status word
+constexpr size_t kHeaderBytes = 8192;  // CurveStats, status word, slice counter, slice statistics
 constexpr int64_t kMaxSamples = int64_t(1) << 19;      // 524,288 samples
 constexpr size_t kRecordBytes = size_t(kMaxSamples) * 32;      // 16 MiB of phase records
 constexpr size_t kPartialBytes = size_t(48) << 20;             // 48 MiB of partial sums
-constexpr size_t kScratchBytes = kHeaderBytes + kRecordBytes + kPartialBytes;  // 64 MiB + 256 B
+constexpr size_t kScratchBytes = kHeaderBytes + kRecordBytes + kPartialBytes;  // 64 MiB + 8 KiB
 
 // Host code sees this name only as a host-side stand-in; the device address
 // comes from cudaGetSymbolAddress, once per device.
@@ -84,15 +84,19 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     cudaStream_t st = (cudaStream_t)cuda_stream;
     lsp::CurveStats* stats = (lsp::CurveStats*)base;
     int* status = (int*)(base + sizeof(lsp::CurveStats));
+    unsigned* counter = (unsigned*)(base + sizeof(lsp::CurveStats) + 8);
+    lsp::StatPart* sparts = (lsp::StatPart*)(base + 256);
+    static_assert(256 + sizeof(lsp::StatPart) * lsp::kMaxStatSlices <= kHeaderBytes, "header too small");
     uint4* recA = (uint4*)(base + kHeaderBytes);
     float4* recB = (float4*)(base + kHeaderBytes + size_t(kMaxSamples) * 16);
     float* part = (float*)(base + kHeaderBytes + kRecordBytes);
 
-    // Launch shape of the recurrence path: strips of 16 frequencies; the N_t
-    // split fills the SMs but never needs more partial sums than fit.
+    // Launch shape of the default (three-term recurrence) path: strips of 24
+    // frequencies; the N_t split fills the SMs but never needs more partial
+    // sums than fit.
     lsp::MainShape s{};
-    s.mode = 2;
-    s.F = 16;
+    s.mode = lsp::kModeRecur3;
+    s.F = 24;
     const int64_t per_block = lsp::freqs_per_block(s.F);
     s.nfb = (int)((N_f + per_block - 1) / per_block);
     s.nf_pad = (int64_t)s.nfb * per_block;
@@ -106,11 +110,13 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     s.chunk = (N_t + split - 1) / split;
     s.split = (int)((N_t + s.chunk - 1) / s.chunk);
 
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);  // the shared word keeps old flags
-    if (e == cudaSuccess) e = lsp::launch_prep_stats(t, X, nullptr, N_t, 1, stats, status, st);
+    // the shared array keeps the last call's contents: clear the status word
+    // and the slice counter, which must start at zero
+    cudaError_t e = cudaMemsetAsync(status, 0, 16, st);
+    if (e == cudaSuccess) e = lsp::launch_prep_stats(t, X, nullptr, N_t, 1, stats, status, sparts, counter, st);
     if (e == cudaSuccess)
         e = lsp::launch_prep_records(t, X, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats, recA, recB,
-                                     nullptr, st);
+                                     nullptr, nullptr, st);
     if (e == cudaSuccess) e = lsp::launch_main(s, recA, recB, nullptr, N_t, N_f, f_0, df, part, P_out, st);
     if (e == cudaSuccess && s.split > 1) e = lsp::launch_finalize(s, part, N_t, N_f, P_out, st);
     if (e != cudaSuccess) {

@@ -1,0 +1,143 @@
+// noise.cu -- Gaussian noise for Monte-Carlo periodograms (Sec. 6.2: the
+// statistics of peak heights under pure noise, e.g. the number of independent
+// frequencies behind Eq. 3, are estimated from many noise periodograms).
+//
+// Sample j of realization r of curve c is drawn from Philox-4x32-10 (Salmon,
+// Moraes, Dror & Shaw 2011) with counter (j/4, c, r, 0) and key (seed low,
+// seed high): every value is a pure function of (seed, c, r, j), so runs are
+// reproducible and resumable.  Each 32-bit word w becomes the uniform
+// u = (2 (w >> 9) + 1) 2^-24 in (0, 1) (exact in FP32), and the Box-Muller
+// transform (Box & Muller 1958) turns (u0, u1), (u2, u3) into four N(0, 1)
+// values: sqrt(-2 ln u_a) (cos, sin)(2 pi u_b).
+#include <cfloat>
+
+#include "lsp_kernels.cuh"
+
+namespace lsp {
+namespace {
+
+constexpr int kNoiseThreads = 256;
+
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                             uint32_t k0, uint32_t k1) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        philox_round(c0, c1, c2, c3, k0, k1);
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ float unit_uniform(uint32_t w) { return (float)(2u * (w >> 9) + 1u) * 0x1p-24f; }
+
+// Four N(0,1) values of Philox block `blk` of (curve, real).
+__device__ __forceinline__ float4 normals4(uint64_t seed, uint32_t blk, uint32_t curve, uint32_t real) {
+    const uint4 w = philox4x32_10(blk, curve, real, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const float r0 = sqrtf(-2.f * logf(unit_uniform(w.x)));
+    const float r1 = sqrtf(-2.f * logf(unit_uniform(w.z)));
+    float s0, c0, s1, c1;
+    sincospif(2.f * unit_uniform(w.y), &s0, &c0);
+    sincospif(2.f * unit_uniform(w.w), &s1, &c1);
+    return make_float4(r0 * c0, r0 * s0, r1 * c1, r1 * s1);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) sh[32] = r;
+    __syncthreads();
+    return sh[32];
+}
+
+// Raw N(0,1) values of one (curve, realization), samples [0, n).
+__global__ void __launch_bounds__(kNoiseThreads)
+noise_raw_kernel(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float* __restrict__ out) {
+    const int64_t nb = (n + 3) / 4;
+    for (int64_t blk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; blk < nb;
+         blk += (int64_t)gridDim.x * blockDim.x) {
+        const float4 z = normals4(seed, (uint32_t)blk, curve, real);
+        const int64_t j = blk * 4;
+        out[j] = z.x;
+        if (j + 1 < n) out[j + 1] = z.y;
+        if (j + 2 < n) out[j + 2] = z.z;
+        if (j + 3 < n) out[j + 3] = z.w;
+    }
+}
+
+// One CTA per (curve, realization): draw the noise into xr, then normalize it
+// in place to zero mean and unit population variance (Sec. 3), mean and
+// variance in FP64 over two passes.
+__global__ void __launch_bounds__(kNoiseThreads)
+noise_prep_kernel(const int64_t* __restrict__ off, const uint64_t* __restrict__ seed_p, int64_t total,
+                  float* __restrict__ xr) {
+    __shared__ double sh[33];
+    const int c = blockIdx.x, r = blockIdx.y;
+    const int64_t b = off[c], n = off[c + 1] - off[c];
+    float* x = xr + (size_t)r * (size_t)total + b;
+    const uint64_t seed = *seed_p;
+    double s = 0.0;
+    for (int64_t blk = threadIdx.x; blk * 4 < n; blk += blockDim.x) {
+        const float4 z = normals4(seed, (uint32_t)blk, (uint32_t)c, (uint32_t)r);
+        const int64_t j = blk * 4;
+        x[j] = z.x;
+        s += z.x;
+        if (j + 1 < n) { x[j + 1] = z.y; s += z.y; }
+        if (j + 2 < n) { x[j + 2] = z.z; s += z.z; }
+        if (j + 3 < n) { x[j + 3] = z.w; s += z.w; }
+    }
+    __syncthreads();
+    const double mean = block_sum(s, sh) / (double)n;
+    double v = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double d = (double)x[j] - mean;
+        v = fma(d, d, v);
+    }
+    const double var = block_sum(v, sh) / (double)n;
+    const double inv_sd = var > 0.0 ? 1.0 / sqrt(var) : 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) x[j] = (float)(((double)x[j] - mean) * inv_sd);
+}
+
+}  // namespace
+
+cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float* out, cudaStream_t st) {
+    const int64_t nb = (n + 3) / 4;
+    int64_t blocks = (nb + kNoiseThreads - 1) / kNoiseThreads;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    noise_raw_kernel<<<(unsigned)blocks, kNoiseThreads, 0, st>>>(seed, curve, real, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise_prep(const int64_t* off, int n_curves, int n_real, const uint64_t* seed_dev,
+                              int64_t total, float* xr, cudaStream_t st) {
+    dim3 grid((unsigned)n_curves, (unsigned)n_real);
+    noise_prep_kernel<<<grid, kNoiseThreads, 0, st>>>(off, seed_dev, total, xr);
+    return cudaGetLastError();
+}
+
+}  // namespace lsp

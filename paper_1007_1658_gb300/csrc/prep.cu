@@ -51,22 +51,30 @@ __device__ double block_min(double v, double* sh) {
     return sh[32];
 }
 
-// One CTA per curve: t_ref = min t, mean and population variance of X in
-// two passes, non-finite detection.  A degenerate curve gets inv_sd = NaN, so
-// its periodogram comes out NaN and the status word says why.
+// Statistics of one curve, or of one slice of it (G CTAs per curve): t_ref =
+// min t, mean and population variance of X (two passes over the slice, FP64),
+// non-finite detection.  With G > 1 each CTA leaves (n, mean, M2, min t) of
+// its slice and the last CTA to finish merges the G slices in slice order
+// (Chan, Golub & LeVeque's pairwise update), so the result does not depend
+// on which CTA finishes last.  A degenerate curve gets inv_sd = NaN, so its
+// periodogram comes out NaN and the status word says why.
 __global__ void __launch_bounds__(kStatsThreads)
 prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
                   const int64_t* __restrict__ off, int64_t n0, CurveStats* __restrict__ stats,
-                  int* __restrict__ status) {
+                  int* __restrict__ status, StatPart* __restrict__ parts, unsigned* __restrict__ counters) {
     __shared__ double sh[33];
-    const int c = blockIdx.x;
+    __shared__ int last;
+    const int c = blockIdx.y, g = blockIdx.x, G = gridDim.x;
     const int64_t b = off ? off[c] : 0;
     const int64_t e = off ? off[c + 1] : n0;
     const int64_t n = e - b;
+    const int64_t L = (n + G - 1) / G;
+    const int64_t sb = min(e, b + (int64_t)g * L);
+    const int64_t se = min(e, sb + L);
     double s = 0.0, tmin = DBL_MAX;
     int bad = 0;
-    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const double x = X[j], tj = t[j];
+    for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
+        const double x = X ? X[j] : 0.0, tj = t[j];
         bad |= !(isfinite(x) && isfinite(tj));
         s += x;
         tmin = fmin(tmin, tj);
@@ -74,15 +82,56 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
     bad = __syncthreads_or(bad);
     s = block_sum(s, sh);
     tmin = block_min(tmin, sh);
-    const double mean = s / (double)n;
+    const double cnt = (double)(se - sb);
+    const double mean_g = cnt > 0 ? s / cnt : 0.0;
     double v = 0.0;
-    for (int64_t j = b + threadIdx.x; j < e; j += blockDim.x) {
-        const double d = X[j] - mean;
-        v = fma(d, d, v);
+    if (X) {
+        for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
+            const double d = X[j] - mean_g;
+            v = fma(d, d, v);
+        }
     }
     v = block_sum(v, sh);
+    double tot_n = cnt, mean = mean_g, m2 = v;
+    if (G > 1) {
+        if (threadIdx.x == 0) {
+            StatPart* pp = parts + (size_t)c * G + g;
+            pp->n = cnt;
+            pp->mean = mean_g;
+            pp->m2 = v;
+            pp->tmin = tmin;
+            pp->bad = bad;
+            __threadfence();
+            last = atomicAdd(&counters[c], 1u) == (unsigned)(G - 1);
+        }
+        __syncthreads();
+        if (!last) return;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            tot_n = 0.0;
+            mean = 0.0;
+            m2 = 0.0;
+            tmin = DBL_MAX;
+            bad = 0;
+            const StatPart* pp = parts + (size_t)c * G;
+            for (int q = 0; q < G; ++q) {
+                const double nb = __ldcg(&pp[q].n);
+                if (nb <= 0.0) continue;
+                const double mb = __ldcg(&pp[q].mean), m2b = __ldcg(&pp[q].m2);
+                const double nn = tot_n + nb;
+                const double d = mb - mean;
+                mean += d * (nb / nn);
+                m2 += m2b + d * d * (tot_n * nb / nn);
+                tot_n = nn;
+                tmin = fmin(tmin, __ldcg(&pp[q].tmin));
+                bad |= __ldcg(&pp[q].bad);
+            }
+            counters[c] = 0u;  // ready for the next call
+        }
+    }
     if (threadIdx.x == 0) {
-        const double var = v / (double)n;
+        // without X (noise drawn later) only t_ref matters: unit scale
+        const double var = X ? m2 / (double)n : 1.0;
         const bool ok = !bad && var > 0.0 && n >= 2;
         CurveStats r;
         r.mean = mean;
@@ -113,7 +162,8 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
                     const int64_t* __restrict__ off, int64_t n0,
                     const double* __restrict__ f0a, const double* __restrict__ dfa,
                     double f0s, double dfs, const CurveStats* __restrict__ stats,
-                    uint4* __restrict__ recA, float4* __restrict__ recB, float2* __restrict__ recN) {
+                    uint4* __restrict__ recA, float4* __restrict__ recB, float2* __restrict__ recN,
+                    float* __restrict__ xout) {
     const int c = blockIdx.y;
     const int64_t b = off ? off[c] : 0;
     const int64_t e = off ? off[c + 1] : n0;
@@ -130,31 +180,42 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
         const double turn = (double)(int64_t)u * 0x1p-64;
         double sn, cs;
         sincospi(2.0 * turn, &sn, &cs);
-        const float xh = (float)((X[j] - st.mean) * st.inv_sd);
+        const float xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
         recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
         recB[j] = make_float4(xh, (float)cs, (float)sn, __uint_as_float(du));
         if (recN) recN[j] = make_float2(xh, __double2float_rn(tt));
+        if (xout) xout[j] = xh;
     }
 }
 
 }  // namespace
 
+int prep_stats_slices(int n_curves, int64_t n0) {
+    if (n_curves > 1) return 1;
+    int64_t g = n0 / 8192;
+    return (int)(g < 1 ? 1 : (g > kMaxStatSlices ? kMaxStatSlices : g));
+}
+
 cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
-                              int n_curves, CurveStats* stats, int* status, cudaStream_t st) {
-    prep_stats_kernel<<<n_curves, kStatsThreads, 0, st>>>(t, X, off, n0, stats, status);
+                              int n_curves, CurveStats* stats, int* status, StatPart* parts,
+                              unsigned* counters, cudaStream_t st) {
+    // without slice scratch every curve gets one CTA
+    const int G = (parts && counters) ? prep_stats_slices(n_curves, n0) : 1;
+    dim3 grid((unsigned)G, (unsigned)n_curves);
+    prep_stats_kernel<<<grid, kStatsThreads, 0, st>>>(t, X, off, n0, stats, status, parts, counters);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
-                                uint4* recA, float4* recB, float2* recN, cudaStream_t st) {
+                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st) {
     int64_t bx = (max_n + 255) / 256;
     if (bx > 4096) bx = 4096;
     if (bx < 1) bx = 1;
     dim3 grid((unsigned)bx, (unsigned)n_curves);
     prep_records_kernel<<<grid, 256, 0, st>>>(t, X, off, n0, f0, df, f0_single, df_single, stats,
-                                              recA, recB, recN);
+                                              recA, recB, recN, xout);
     return cudaGetLastError();
 }
 

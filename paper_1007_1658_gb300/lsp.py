@@ -23,7 +23,7 @@ _lock = threading.Lock()
 
 OK, ERR_INVALID_ARG, ERR_DEGENERATE, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_MODEL, \
     ERR_UNSUPPORTED = range(9)
-SINCOS_AUTO, SINCOS_MUFU, SINCOS_RECUR = 0, 1, 2
+SINCOS_AUTO, SINCOS_MUFU, SINCOS_RECUR, SINCOS_RECUR3 = 0, 1, 2, 3
 PHASE_FIXED64, PHASE_NAIVE_FP32 = 0, 1
 
 _NAMES = {0: "OK", 1: "INVALID_ARG", 2: "DEGENERATE", 3: "NONFINITE", 4: "OOM", 5: "CUDA",
@@ -84,6 +84,9 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_batch"):
         lib.lsp_batch.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
         lib.lsp_batch.restype = ctypes.c_int
+    if hasattr(lib, "lsp_noise"):
+        lib.lsp_noise.argtypes = [p, u64, i32, i32, i64, p]
+        lib.lsp_noise.restype = ctypes.c_int
 
 
 def options(**kw) -> lsp_options:
@@ -162,6 +165,34 @@ class Context:
         n = t.numel() if hasattr(t, "numel") else t.size
         self._check(self._lib.lsp_periodogram(self.h, _ptr(t), _ptr(X), int(n), float(f0), float(df), nf,
                                               _ptr(out)))
+        return out
+
+    def batch(self, t_off, t, f0, df, nf, X=None, seed=0, n_real=1, P_out=None, P_off=None,
+              maxP=None, argmax=None):
+        """lsp_batch: many curves (CSR t_off/t), per-curve grids f0/df/nf; X None =
+        Philox noise (n_real realizations).  Outputs are filled in place; a
+        missing maxP/argmax is allocated on t's device (or host) and returned."""
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        if maxP is None and argmax is None and P_out is None:
+            if hasattr(t, "data_ptr"):
+                import torch
+                maxP = torch.empty(n_real * n, dtype=torch.float32, device=t.device)
+                argmax = torch.empty(n_real * n, dtype=torch.int32, device=t.device)
+            else:
+                maxP = np.empty(n_real * n, dtype=np.float32)
+                argmax = np.empty(n_real * n, dtype=np.int32)
+        self._bind_stream()
+        self._check(self._lib.lsp_batch(self.h, n, _ptr(t_off), _ptr(t), _ptr(X), ctypes.c_uint64(int(seed)),
+                                        int(n_real), _ptr(f0), _ptr(df), _ptr(nf), _ptr(P_out), _ptr(P_off),
+                                        _ptr(maxP), _ptr(argmax)))
+        return maxP, argmax
+
+    def noise(self, seed, curve, real, n, out=None):
+        """lsp_noise: the raw N(0,1) values lsp_batch draws for (seed, curve, real)."""
+        if out is None:
+            out = np.empty(int(n), dtype=np.float32)
+        self._bind_stream()
+        self._check(self._lib.lsp_noise(self.h, ctypes.c_uint64(int(seed)), int(curve), int(real), int(n), _ptr(out)))
         return out
 
     def sync(self, timeout_s: float = -1.0):

@@ -45,11 +45,14 @@ def _run(ctx, t, X, f0, df, nf, **opts):
     return P.cpu().numpy().astype(np.float64)
 
 
-MODES = [dict(sincos_mode=2), dict(sincos_mode=1)]
+MODES = [dict(sincos_mode=2), dict(sincos_mode=1), dict(sincos_mode=3)]
 
 
 @pytest.mark.parametrize("opts", MODES + [dict(sincos_mode=2, freqs_per_thread=4),
-                                          dict(sincos_mode=2, freqs_per_thread=8),
+                                          dict(sincos_mode=2, freqs_per_thread=16),
+                                          dict(sincos_mode=3, freqs_per_thread=16),
+                                          dict(sincos_mode=3, freqs_per_thread=8),
+                                          dict(sincos_mode=2, freqs_per_thread=24),
                                           dict(sincos_mode=1, freqs_per_thread=16),
                                           dict(sincos_mode=2, split=1),
                                           dict(sincos_mode=1, split=7)])
@@ -65,7 +68,7 @@ def test_plain_1k_full_grid(ctx, opts):
 
 @pytest.mark.parametrize("n,nf", [(2, 7), (3, 1), (5, 64), (255, 511), (256, 512), (257, 513),
                                   (1000, 2049), (4099, 2048), (1023, 4097), (600, 1)])
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_ragged_sizes(ctx, n, nf, mode):
     rng = np.random.default_rng(n * 7919 + nf)
     t = np.sort(rng.uniform(0, 37.0, n))
@@ -82,7 +85,7 @@ def test_ragged_sizes(ctx, n, nf, mode):
         assert_parity(got, ref, what="n=%d nf=%d mode=%d" % (n, nf, mode))
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_even_grid_closed_form_on_gpu(ctx, mode):
     # Eq. 1-2 closed form: P = N/2 at the injected Fourier frequency, 0 at the others.
     N, m = 1024, 137
@@ -184,8 +187,8 @@ def _window_peaks(c, ks, ref):
     return np.array(order, dtype=np.int64)
 
 
-@pytest.mark.parametrize("name,mode", [("gapped_100k", 2), ("gapped_100k", 1), ("cadence_65k", 2),
-                                       ("cadence_65k", 1)])
+@pytest.mark.parametrize("name,mode", [("gapped_100k", 2), ("gapped_100k", 1), ("gapped_100k", 3),
+                                       ("cadence_65k", 2), ("cadence_65k", 1), ("cadence_65k", 3)])
 def test_full_size_sampled(ctx, name, mode):
     from paper_1007_1658_gb300 import synth
     c = synth.WORKLOADS[name]()
