@@ -236,23 +236,29 @@ def run_gpu(args, rank, world, dist):
         return 0
     peaks, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mode = args.mode if args.mode else lsp.SINCOS_RECUR
-    terms_per_clk = 16.0 if mode == lsp.SINCOS_RECUR else 8.0
+    mode = args.mode if args.mode else lsp.SINCOS_RECUR3
+    F = args.F if args.F else {lsp.SINCOS_MUFU: 8, lsp.SINCOS_RECUR: 16, lsp.SINCOS_RECUR3: 24}[mode]
+    # algorithmic work per term on the bounding pipe (roof in terms per clock per SM)
+    roof = {lsp.SINCOS_MUFU: (2, "SFU (MUFU): 2 sin/cos ops per term, 16 ops/clk/SM", 16.0 / 2),
+            lsp.SINCOS_RECUR: (8, "FMA pipe: 4 accumulate + 4 rotation FP32 ops per term, 128/clk/SM", 128.0 / 8),
+            lsp.SINCOS_RECUR3: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 ops per term, 128/clk/SM",
+                                128.0 / 6)}[mode]
+    terms_per_clk = roof[2]
     peak = terms_per_clk * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
-    kernel = "ls_main_kernel<16,2>" if mode == lsp.SINCOS_RECUR else "ls_main_kernel<8,1>"
+    kernel = "ls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4}[mode])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N_t": int(c.t.size), "N_f": int(c.nf), "terms_per_step": terms,
-                   "sincos": "recurrence" if mode == lsp.SINCOS_RECUR else "mufu", "phase": "fixed64",
+                   "sincos": {1: "mufu", 2: "recurrence", 3: "three-term recurrence"}[mode], "F": F,
+                   "phase": "fixed64",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "frequency shards x%d" % world},
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e9, "peak": peak / 1e9,
                      "unit": "Gterms/s", "frac": achieved / peak, "traffic": _recorded_traffic(kernel),
-                     "peak_basis": "%s: %d terms/clk/SM x %d SMs x %.0f MHz (%s sm_max_mhz)" % (
-                         "FMA pipe, 8 FP32 ops/term" if mode == lsp.SINCOS_RECUR else "SFU, 2 MUFU ops/term",
-                         terms_per_clk, sms, peaks["sm_max_mhz"], peak_src),
+                     "peak_basis": "%s: %.2f terms/clk/SM x %d SMs x %.0f MHz (%s sm_max_mhz)" % (
+                         roof[1], terms_per_clk, sms, peaks["sm_max_mhz"], peak_src),
                      "main_ms": float(np.mean(main_ms))},
         "e2e": None if e2e_val is None else {
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c.t.nbytes + c.X.nbytes),
@@ -288,9 +294,73 @@ def _e2e(lsp, torch, c, f0, local, stream, args, world):
 
 
 def run_batch_bench(ctx, torch, dev, stream, args):
-    """Config-4 Monte-Carlo batch: one graph-captured persistent launch vs one
-    lsp_periodogram launch per curve (filled in once lsp_batch exists)."""
-    return None
+    """Monte-Carlo batch (4096 pure-noise curves, N_t log-uniform in
+    [200, 20000], gapped patterns, N_f = 2 N_t): one graph-captured persistent
+    launch (lsp_batch, noise drawn on the device, per-curve max P) against the
+    plain form, one lsp_periodogram call per curve on the same stream (same
+    noise values, copied in beforehand; its per-curve maxima are not counted)."""
+    from paper_1007_1658_gb300 import lsp, synth
+    b = synth.noise_batch(n_curves=args.batch_curves)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    off, t, f0, df, nf = d(b.t_off), d(b.t), d(b.f0), d(b.df), d(b.nf)
+    maxP = torch.empty(b.n, dtype=torch.float32, device=dev)
+    arg = torch.empty(b.n, dtype=torch.int32, device=dev)
+    bctx = lsp.Context(dev.index or 0, stream=stream)
+    seed = 1234
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            bctx.batch(off, t, f0, df, nf, seed=seed, maxP=maxP, argmax=arg)
+        bctx.sync(300.0)
+        reps = max(2, args.batch_reps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for r in range(reps):
+            bctx.batch(off, t, f0, df, nf, seed=seed + r, maxP=maxP, argmax=arg)
+        e1.record(stream)
+        bctx.sync(300.0)
+    torch.cuda.synchronize(dev)
+    batch_ms = e0.elapsed_time(e1) / reps
+    # plain form: the same noise (realization 0 of seed 1234), one call per curve
+    X = torch.empty(b.t.size, dtype=torch.float64, device=dev)
+    tmp = torch.empty(int(np.diff(b.t_off).max()), dtype=torch.float32, device=dev)
+    for c in range(b.n):
+        n = int(b.t_off[c + 1] - b.t_off[c])
+        bctx.noise(seed, c, 0, n, out=tmp[:n])
+        X[int(b.t_off[c]):int(b.t_off[c + 1])] = tmp[:n].double()
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    P = torch.empty(int(P_off[-1]), dtype=torch.float32, device=dev)
+    pctx = lsp.Context(dev.index or 0, stream=stream)
+    views = [(t[int(b.t_off[c]):int(b.t_off[c + 1])], X[int(b.t_off[c]):int(b.t_off[c + 1])],
+              float(b.f0[c]), float(b.df[c]), int(b.nf[c]), P[int(P_off[c]):int(P_off[c + 1])]) for c in range(b.n)]
+    with torch.cuda.stream(stream):
+        for v in views[:64]:
+            pctx.periodogram(v[0], v[1], v[2], v[3], v[4], out=v[5])
+        pctx.sync(300.0)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        launches = 0
+        for v in views:
+            pctx.periodogram(v[0], v[1], v[2], v[3], v[4], out=v[5])
+            launches += pctx.last_launch_count()
+        e3.record(stream)
+        pctx.sync(300.0)
+    torch.cuda.synchronize(dev)
+    plain_ms = e2.elapsed_time(e3)
+    # the two forms agree on the maxima (same noise, same arithmetic up to summation order)
+    Pn = P.cpu().numpy()
+    pmax = np.array([Pn[P_off[c]:P_off[c + 1]].max() for c in range(b.n)])
+    bctx.batch(off, t, f0, df, nf, seed=seed, maxP=maxP, argmax=arg)
+    bctx.sync(300.0)
+    agree = float(np.max(np.abs(pmax - maxP.cpu().numpy()) / pmax))
+    bctx.close()
+    pctx.close()
+    return {"workload": "noise_batch: %d pure-noise curves, N_t log-U[200,20000], N_f = 2 N_t" % b.n,
+            "terms": b.terms, "graph_ms": batch_ms, "curves_per_s": b.n / (batch_ms * 1e-3),
+            "terms_per_s": b.terms / (batch_ms * 1e-3), "plain_ms": plain_ms,
+            "plain_curves_per_s": b.n / (plain_ms * 1e-3), "plain_terms_per_s": b.terms / (plain_ms * 1e-3),
+            "plain_launches": launches, "batch_launches": 1, "speedup_vs_plain": plain_ms / batch_ms,
+            "max_rel_diff_batch_vs_plain": agree}
 
 
 def main():
@@ -308,6 +378,8 @@ def main():
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--nf", type=int, default=0, help="override N_f (smaller profiling case)")
+    ap.add_argument("--batch-curves", type=int, default=4096)
+    ap.add_argument("--batch-reps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

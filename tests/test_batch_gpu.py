@@ -1,0 +1,167 @@
+"""GPU parity of the batched Monte-Carlo path (lsp_batch) and of its noise (lsp_noise).
+
+Noise: the device's FP32 Philox-4x32-10 + Box-Muller values against the
+oracle's FP64 evaluation of the same counter-based generator (same integers,
+so the normals agree to FP32 rounding).  Periodograms: every batch result
+against the FP64 oracle evaluated on the oracle's own noise, with the parity
+tolerance of the single-curve tests (|dP| <= 1e-4 max P per periodogram);
+argmax must hit a bin whose oracle value is within that tolerance of the
+oracle's maximum.  A statistical pin checks the whole engine against the beta
+law behind Eq. 3.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from tests.parity import TOL_ABS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lsp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1007_1658_gb300 import build, lsp as L
+    build.build()
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lsp):
+    c = lsp.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a, dtype=None):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=dtype)).cuda()
+
+
+@pytest.mark.parametrize("seed,curve,real,n", [(0, 0, 0, 1001), (2024, 3, 7, 4099), (2**40 + 5, 4095, 1, 17)])
+def test_noise_matches_oracle_generator(ctx, seed, curve, real, n):
+    got = ctx.noise(seed, curve, real, n).astype(np.float64)
+    ref = oracle.noise(seed, curve, real, n)
+    assert np.all(np.abs(got - ref) <= 4e-6 * np.maximum(1.0, np.abs(ref)))
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    ctx.noise(seed, curve, real, n, out=d)
+    ctx.sync(30.0)
+    assert np.array_equal(d.cpu().numpy().astype(np.float64), got)
+
+
+def _small_batch(n_curves=12, seed=5):
+    from paper_1007_1658_gb300 import synth
+    return synth.noise_batch(n_curves=n_curves, seed=seed, nt_min=40, nt_max=900, t_min=5.0, t_max=80.0)
+
+
+def _oracle_noise_curve(b, seed, c, r):
+    t = b.curve_t(c)
+    X = oracle.noise(seed, c, r, t.size)
+    return t, X
+
+
+@pytest.mark.parametrize("mode", [3, 2, 1])
+def test_noise_batch_matches_oracle(ctx, lsp, mode):
+    b = _small_batch()
+    seed, n_real = 99, 3
+    ctx.set_options(sincos_mode=mode)
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    P = torch.empty(n_real * int(P_off[-1]), dtype=torch.float32, device="cuda")
+    maxP, argmax = ctx.batch(_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf), seed=seed,
+                             n_real=n_real, P_out=P, P_off=_dev(P_off),
+                             maxP=torch.empty(n_real * b.n, device="cuda"),
+                             argmax=torch.empty(n_real * b.n, dtype=torch.int32, device="cuda"))
+    ctx.sync(60.0)
+    P = P.cpu().numpy().astype(np.float64)
+    maxP = maxP.cpu().numpy()
+    argmax = argmax.cpu().numpy()
+    for r in range(n_real):
+        for c in range(b.n):
+            t, X = _oracle_noise_curve(b, seed, c, r)
+            ref = oracle.periodogram(t, X, b.f0[c], b.df[c], b.nf[c])
+            got = P[r * P_off[-1] + P_off[c]: r * P_off[-1] + P_off[c] + b.nf[c]]
+            scale = ref.max()
+            assert np.max(np.abs(got - ref)) <= TOL_ABS * scale, (r, c)
+            i = r * b.n + c
+            assert abs(maxP[i] - scale) <= TOL_ABS * scale
+            assert 0 <= argmax[i] < b.nf[c] and ref[argmax[i]] >= scale * (1 - 2 * TOL_ABS)
+            assert maxP[i] == np.float32(got[argmax[i]])
+
+
+def test_measured_batch_host_and_device_paths(ctx, lsp):
+    b = _small_batch(n_curves=7, seed=8)
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=b.t.size) + 3.0
+    for c in range(b.n):  # a line in every curve
+        s = slice(b.t_off[c], b.t_off[c + 1])
+        X[s] += 2.0 * np.sin(2 * np.pi * (0.3 + 0.05 * c) * b.t[s])
+    ctx.set_options(sincos_mode=3)
+    maxP_d, arg_d = ctx.batch(_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf), X=_dev(X))
+    ctx.sync(60.0)
+    maxP_h, arg_h = ctx.batch(b.t_off, b.t, b.f0, b.df, b.nf, X=X)  # numpy in and out
+    assert np.array_equal(maxP_d.cpu().numpy(), maxP_h) and np.array_equal(arg_d.cpu().numpy(), arg_h)
+    for c in range(b.n):
+        s = slice(b.t_off[c], b.t_off[c + 1])
+        ref = oracle.periodogram(b.t[s], X[s], b.f0[c], b.df[c], b.nf[c])
+        assert abs(maxP_h[c] - ref.max()) <= TOL_ABS * ref.max()
+        assert ref[arg_h[c]] >= ref.max() * (1 - 2 * TOL_ABS)
+
+
+def test_graph_replay_is_deterministic_and_seeded(ctx):
+    b = _small_batch(n_curves=20, seed=11)
+    args = (_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf))
+    ctx.set_options(sincos_mode=3)
+    out = [torch.empty(2 * b.n, device="cuda") for _ in range(3)]
+    arg = [torch.empty(2 * b.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    for i, s in enumerate((1, 1, 2)):
+        ctx.batch(*args, seed=s, n_real=2, maxP=out[i], argmax=arg[i])
+    ctx.sync(60.0)
+    assert torch.equal(out[0], out[1]) and torch.equal(arg[0], arg[1])
+    assert not torch.equal(out[0], out[2])
+    # realization 1 of seed 1 is its own stream, not a copy of realization 0
+    assert not torch.equal(out[0][:b.n], out[0][b.n:])
+
+
+def test_edge_curves(ctx, lsp):
+    # a 2-sample curve, a curve with no frequencies, and a 3-sample curve
+    t = np.array([0.0, 1.0, 0.0, 0.5, 2.0, 0.0, 0.3, 0.9], np.float64)
+    off = np.array([0, 2, 5, 8], np.int64)
+    X = np.array([1.0, -1.0, 0.2, 0.9, -1.3, 1.0, 2.0, 0.5])
+    f0 = np.array([0.1, 0.1, 0.05])
+    df = np.array([0.1, 0.1, 0.05])
+    nf = np.array([5, 0, 9], np.int64)
+    maxP, arg = ctx.batch(off, t, f0, df, nf, X=X)
+    assert maxP[1] == 0.0 and arg[1] == -1
+    for c in (0, 2):
+        s = slice(off[c], off[c + 1])
+        ref = oracle.periodogram(t[s], X[s], f0[c], df[c], nf[c])
+        assert abs(maxP[c] - ref.max()) <= 1e-3 * max(1.0, ref.max())
+    with pytest.raises(lsp.LspError) as e:
+        ctx.batch(off, t, f0, df, nf, X=np.array([1.0, 1.0, 0.2, 0.9, -1.3, 1.0, 2.0, 0.5]))
+        ctx.sync(10.0)
+    assert e.value.status == lsp.ERR_DEGENERATE
+    with pytest.raises(lsp.LspError) as e:
+        ctx.batch(np.array([0, 1], np.int64), t[:1], f0[:1], df[:1], nf[:1], X=X[:1])
+    assert e.value.status == lsp.ERR_INVALID_ARG
+    with pytest.raises(lsp.LspError) as e:
+        ctx.batch(off, t, f0, df, nf, X=X, n_real=2)
+    assert e.value.status == lsp.ERR_INVALID_ARG
+
+
+def test_noise_periodograms_follow_the_beta_law(ctx):
+    """Whole-engine statistical pin: even sampling, one Fourier frequency, many
+    noise realizations through lsp_batch -> 2P/N ~ Beta(1, (N-3)/2) (Eq. 3's law)."""
+    N, m, R = 48, 5, 4000
+    t = np.arange(N, dtype=np.float64)
+    off = np.array([0, N], np.int64)
+    P_off = np.array([0, 1], np.int64)
+    P = np.empty(R, np.float32)
+    ctx.set_options(sincos_mode=3)
+    ctx.batch(off, t, np.array([m / N]), np.array([1.0 / N]), np.array([1], np.int64), seed=7, n_real=R,
+              P_out=P, P_off=P_off)
+    z = 2 * P.astype(np.float64) / N
+    assert stats.kstest(z, stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
