@@ -178,7 +178,7 @@ def run_reference(args, rank, world):
 
 def run_gpu(args, rank, world, dist):
     import torch
-    from paper_1007_1658_gb300 import lsp, synth
+    from paper_1007_1658_gb300 import lsp, shard, synth
 
     local = _env_int("LOCAL_RANK", 0)
     torch.cuda.set_device(local)
@@ -186,7 +186,7 @@ def run_gpu(args, rank, world, dist):
     c = synth.gapped_100k()
     if args.nf:
         c.nf = int(args.nf)  # smaller case of the same kernel (profiling captures)
-    f0 = c.f0 + rank * c.nf * c.df  # this rank's block of the grid
+    f0, _, _ = shard.weak_block(c.f0, c.df, c.nf, rank, world)  # this rank's block of the grid
     terms = c.t.size * c.nf
     t_d = torch.from_numpy(c.t).to(dev)
     X_d = torch.from_numpy(c.X).to(dev)
@@ -220,10 +220,7 @@ def run_gpu(args, rank, world, dist):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-    if dist:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(total_ms, dist, dev)
     value = world * terms * args.steps / (total_ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers (copies inside)

@@ -73,7 +73,8 @@ typedef struct lsp_options {
     int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|16|24 */
     int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
-    int32_t reserved[7];      /* must be zero                                          */
+    int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */
+    int32_t reserved[6];      /* must be zero                                          */
 } lsp_options;
 
 /* Fill *opt with the defaults (AUTO sin/cos, FIXED64 phase, automatic launch shape). */
@@ -162,6 +163,17 @@ lsp_status lsp_grid(double t_min, double t_max, int64_t N_t, double F_over, doub
                     double *f_0, double *df, int64_t *N_f);
 
 /*
+ * Autotuner: time the sin/cos modes, strip lengths F (also the recurrence's
+ * re-seed length) and N_t splits on a synthetic series of this size, keep
+ * only candidates within 2e-5 max P of the all-hardware-sin/cos result, and
+ * remember the fastest for this (log2 N_t, log2 N_f) bucket: later calls with
+ * LSP_SINCOS_AUTO and automatic F/split use it.  *chosen (may be NULL)
+ * receives the winning options.  Blocks; allocates temporary buffers.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+lsp_status lsp_autotune(lsp_ctx *ctx, int64_t N_t, int64_t N_f, lsp_options *chosen);
+
+/*
  * Wait for the context's queued work, at most `timeout_s` seconds (< 0: no
  * limit), polling a CUDA event.  Returns TIMEOUT if the deadline passes (the
  * work stays queued), else the first device-detected data error of the calls
@@ -183,6 +195,88 @@ int32_t lsp_last_launch_count(const lsp_ctx *ctx);
 
 /* Text of the last error on this context ("" if none).  Owned by the context. */
 const char *lsp_last_error(const lsp_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned false-alarm surrogate.  Eq. 3 turns a peak height into a false-alarm
+ * probability by treating the N_f grid frequencies as independent; Sec. 6.2
+ * notes that the exponent should be an empirical number of independent
+ * frequencies that depends on the sampling, estimated by Monte-Carlo noise
+ * periodograms.  The surrogate learns, from 32 features of the sampling
+ * pattern, the quantiles of the largest noise peak at the levels
+ * p = 0.05, 0.10, 0.25, 0.50, 0.75, 0.90, 0.95, 0.98, 0.99 (the peak height
+ * whose false-alarm probability is 1 - p).  Network: 32 -> H -> H -> H -> 9,
+ * GELU (exact erf form), FP32 master weights, activations in BF16 (or FP32
+ * with the mlp_fp32 option), and a head on Eq. 3's quantiles: with
+ * e_l = log q_l^Eq3(N_t, N_f) and d_l = e_l - e_{l-1}, log q_1 = e_1 + z_1 and
+ * log q_l = log q_{l-1} + d_l softplus(z_l) / log 2 (monotone in l; z = 0 is
+ * Eq. 3 exactly, and the output layer starts at zero).  Trained with the mean
+ * pinball loss and Adam (beta 0.9/0.999, eps 1e-8).  All of it runs in the
+ * library's kernels.
+ * ------------------------------------------------------------------------- */
+
+#define LSP_FAP_FEATURES 32
+#define LSP_FAP_LEVELS 9
+
+/*
+ * Features of n sampling patterns (CSR t_off/t, sorted times, 2..32769
+ * samples each; grid f_0 >= 0, df > 0, N_f >= 1 as for lsp_batch) into
+ * features[n][32] (FP32).  With T = t_last - t_first, dt the M = N - 1 gaps,
+ * q(p) = sorted(dt)[floor(p (M - 1))], med = q(1/2), f_max = f_0 + (N_f-1) df:
+ *   0 log N, 1 log T, 2 log N_f, 3 log(1/(df T)), 4 log(f_max T / N), 5 log(1 + f_0/df),
+ *   6..10 log(max(q(p), 1e-12 T) / (T/M)), p = 0.05, 0.25, 0.5, 0.75, 0.95,
+ *   11..13 sum of gaps with dt/med > c (1 + 1e-6), over T, c = 2, 10, 100,
+ *   14 max dt / T, 15 fraction of gaps with dt/med > 2 (1 + 1e-6),
+ *   16..23 the 8 highest local maxima of the spectral window
+ *          W(f) = |sum_j exp(2 pi i f t_j)|^2 / N^2 on f_m = m df, m = 1..floor(f_max/df),
+ *          outside the main lobe (f_m T >= 1), ties to lower m, 0 if missing,
+ *   24..31 their f_m / f_max.
+ * Unsorted times give NaN features and NONFINITE from lsp_sync.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+lsp_status lsp_fap_features(lsp_ctx *ctx, int32_t n, const int64_t *t_off, const double *t,
+                            const double *f_0, const double *df, const int64_t *N_f, float *features);
+
+/*
+ * Initialize the network with H hidden units (0: 256) from `seed` (He-normal
+ * hidden weights, zero output layer and biases, Adam moments zero) and set the input standardization
+ * to the column mean / standard deviation of features[n_rows][32].
+ */
+lsp_status lsp_fap_init(lsp_ctx *ctx, int32_t hidden, uint64_t seed, int32_t n_rows, const float *features);
+
+/*
+ * One Adam step on a minibatch of B rows.  Row r = rows[i] (device int32)
+ * takes features[r % n_pat][32], counts[r % n_pat][2] = (N_t, N_f) and the
+ * target targets[r] (a noise-peak maximum); all four tables are device arrays.
+ * loss_out (host or device, may be NULL) receives the minibatch's mean
+ * pinball loss before the step.
+ */
+lsp_status lsp_fap_train_step(lsp_ctx *ctx, int32_t B, const int32_t *rows, int32_t n_pat,
+                              const float *features, const float *counts, const float *targets,
+                              float lr, float *loss_out);
+
+/* Gradient of the mean pinball loss of B rows w.r.t. the flat parameter
+ * vector (layout W1[32][H] b1 W2[H][H] b2 W3[H][H] b3 W4[H][9] b4) into
+ * grad_out, without updating anything; loss_out as above. */
+lsp_status lsp_fap_gradients(lsp_ctx *ctx, int32_t B, const float *features, const float *counts,
+                             const float *targets, float *grad_out, float *loss_out);
+
+/* Quantiles q_out[B][9] of B feature rows with counts (N_t, N_f). */
+lsp_status lsp_fap_eval(lsp_ctx *ctx, int32_t B, const float *features, const float *counts, float *q_out);
+
+/* Features + quantiles of n sampling patterns (N_t >= 4): quantiles_out[n][9]. */
+lsp_status lsp_fap_predict(lsp_ctx *ctx, int32_t n, const int64_t *t_off, const double *t,
+                           const double *f_0, const double *df, const int64_t *N_f,
+                           float *quantiles_out);
+
+/* Flat parameters followed by the 32 feature means and 32 scales; with
+ * out = NULL only *n_out is set.  set_params replaces them (Adam state reset). */
+lsp_status lsp_fap_get_params(lsp_ctx *ctx, float *out, int64_t capacity, int64_t *n_out);
+lsp_status lsp_fap_set_params(lsp_ctx *ctx, int32_t hidden, const float *in, int64_t n);
+
+/* Checkpoint (weights, standardization, Adam moments and step, checksum) to
+ * and from a file; load rejects a file whose checksum does not match. */
+lsp_status lsp_fap_save(lsp_ctx *ctx, const char *path);
+lsp_status lsp_fap_load(lsp_ctx *ctx, const char *path);
 
 /* Release the context, its stream (if owned) and its workspace.  NULL is a no-op. */
 void lsp_destroy(lsp_ctx *ctx);

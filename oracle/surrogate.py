@@ -12,7 +12,8 @@ from features of the sampling pattern.  This module spells out, plainly:
 * ``features``        -- the 32 sampling-pattern features (definitions below)
 * ``eq3_quantile``    -- the level-p quantile of max P under Eq. 3
 * ``mlp_forward`` / ``mlp_backward`` -- 32 -> H -> H -> H -> 9, exact-erf GELU,
-  cumulative-softplus quantile head on top of Eq. 3's quantiles, pinball loss
+  a monotone quantile head that equals Eq. 3's quantiles when the network's
+  output is zero, pinball loss
 * ``adam_step``       -- Kingma & Ba (2015), bias-corrected
 
 Feature definitions (t sorted, N >= 2 samples, grid f_k = f0 + k df, k < N_f):
@@ -21,8 +22,10 @@ Feature definitions (t sorted, N >= 2 samples, grid f_k = f0 + k df, k < N_f):
    0 log N            1 log T             2 log N_f         3 log(1 / (df T))
    4 log(f_max T / N) 5 log(1 + f0 / df)
    6..10 log(max(q(p), 1e-12 T) / (T / M)) for p = 0.05, 0.25, 0.5, 0.75, 0.95
-  11..13 sum of dt over gaps dt > c med, divided by T, for c = 2, 10, 100
-  14 max dt / T       15 fraction of the M gaps with dt > 2 med
+  11..13 sum of dt over gaps with dt / med > c (1 + 1e-6), divided by T, for
+         c = 2, 10, 100 (the margin keeps exact multiples of the cadence, e.g. one
+         dropped sample of an even grid, out of the gaps)
+  14 max dt / T       15 fraction of the M gaps with dt / med > 2 (1 + 1e-6)
   16..23 heights of the 8 highest local maxima of the spectral window
          W(f) = |sum_j exp(2 pi i f t_j)|^2 / N^2 on f_m = m df, m = 1..floor(f_max/df),
          interior points m with W[m] > W[m-1] and W[m] >= W[m+1] and f_m T >= 1
@@ -64,10 +67,11 @@ def features(t, f0, df, nf):
     out[5] = math.log1p(f0 / df)
     for i, p in enumerate((0.05, 0.25, 0.5, 0.75, 0.95)):
         out[6 + i] = math.log(max(q(p), 1e-12 * T) / (T / M))
+    r = dt / med
     for i, c in enumerate((2.0, 10.0, 100.0)):
-        out[11 + i] = dt[dt > c * med].sum() / T
+        out[11 + i] = dt[r > c * (1.0 + 1e-6)].sum() / T
     out[14] = dt.max() / T
-    out[15] = np.count_nonzero(dt > 2.0 * med) / M
+    out[15] = np.count_nonzero(r > 2.0 * (1.0 + 1e-6)) / M
     mw = int(math.floor(f_max / df))
     if mw >= 3:
         fm = np.arange(1, mw + 1) * df
@@ -112,11 +116,12 @@ def sigmoid(x):
 
 
 def init_params(rng, hidden=256, n_in=N_FEATURES, n_out=N_LEVELS):
-    """He-style normal init, zero biases: [W1, b1, W2, b2, W3, b3, W4, b4]."""
+    """He-style normal init of the hidden layers, zero biases, zero output
+    layer (so an untrained network predicts Eq. 3): [W1, b1, ..., W4, b4]."""
     sizes = [n_in, hidden, hidden, hidden, n_out]
     ps = []
-    for a, b in zip(sizes[:-1], sizes[1:]):
-        ps.append(rng.normal(0.0, math.sqrt(2.0 / a), (a, b)))
+    for i, (a, b) in enumerate(zip(sizes[:-1], sizes[1:])):
+        ps.append(rng.normal(0.0, math.sqrt(2.0 / a), (a, b)) if i < 3 else np.zeros((a, b)))
         ps.append(np.zeros(b))
     return ps
 
@@ -124,7 +129,9 @@ def init_params(rng, hidden=256, n_in=N_FEATURES, n_out=N_LEVELS):
 def mlp_forward(params, X, counts, y=None):
     """Quantiles (B x 9) and, with targets y, the mean pinball loss.
 
-    z = MLP(X); o_1 = z_1, o_l = o_{l-1} + softplus(z_l); log q_l = log q_l^Eq3 + o_l."""
+    Head: with e_l = log q_l^Eq3 and d_l = e_l - e_{l-1} > 0 (Eq. 3's log-spacing),
+    log q_1 = e_1 + z_1 and log q_l = log q_{l-1} + d_l softplus(z_l) / log 2.
+    Monotone in l for any z, and z = 0 gives Eq. 3's quantiles exactly."""
     W1, b1, W2, b2, W3, b3, W4, b4 = params
     cache = {"X": X}
     h = X
@@ -135,12 +142,14 @@ def mlp_forward(params, X, counts, y=None):
         cache["a%d" % li] = h
     z = h @ W4 + b4
     cache["z"] = z
-    o = np.empty_like(z)
-    o[:, 0] = z[:, 0]
+    e = np.log(eq3_quantile(counts[:, 0][:, None], counts[:, 1][:, None], LEVELS[None, :]))
+    d = np.diff(e, axis=1)
+    cache["d"] = d
+    lq = np.empty_like(z)
+    lq[:, 0] = e[:, 0] + z[:, 0]
     for l in range(1, N_LEVELS):
-        o[:, l] = o[:, l - 1] + softplus(z[:, l])
-    base = np.log(eq3_quantile(counts[:, 0][:, None], counts[:, 1][:, None], LEVELS[None, :]))
-    q = np.exp(base + o)
+        lq[:, l] = lq[:, l - 1] + d[:, l - 1] * softplus(z[:, l]) / math.log(2.0)
+    q = np.exp(lq)
     cache["q"] = q
     if y is None:
         return q, None, cache
@@ -152,16 +161,16 @@ def mlp_forward(params, X, counts, y=None):
 def mlp_backward(params, cache, y):
     """Gradients of the mean pinball loss w.r.t. [W1, b1, ..., W4, b4]."""
     W1, b1, W2, b2, W3, b3, W4, b4 = params
-    q, z = cache["q"], cache["z"]
+    q, z, d = cache["q"], cache["z"], cache["d"]
     B = q.shape[0]
     u = y[:, None] - q
     dq = np.where(u > 0, -LEVELS, 1.0 - LEVELS) / B     # d loss / d q
-    do = dq * q                                           # q = exp(base + o)
-    # o_l = z_1 + sum_{i=2..l} softplus(z_i): dz_1 = sum_l do_l, dz_i = sigmoid(z_i) sum_{l>=i} do_l
-    tail = np.cumsum(do[:, ::-1], axis=1)[:, ::-1]
+    dlq = dq * q                                          # q = exp(log q)
+    # log q_l = z_1 (+ e_1) + sum_{i=2..l} d_i softplus(z_i) / log 2
+    tail = np.cumsum(dlq[:, ::-1], axis=1)[:, ::-1]
     dz = np.empty_like(z)
     dz[:, 0] = tail[:, 0]
-    dz[:, 1:] = sigmoid(z[:, 1:]) * tail[:, 1:]
+    dz[:, 1:] = tail[:, 1:] * d * sigmoid(z[:, 1:]) / math.log(2.0)
     grads = [None] * 8
     a2 = cache["a2"]
     grads[6] = a2.T @ dz

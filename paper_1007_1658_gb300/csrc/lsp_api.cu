@@ -26,7 +26,7 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
         o->freqs_per_thread != 16 && o->freqs_per_thread != 24)
         return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8, 16 or 24");
     if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "reserved option fields must be zero");
     return LSP_OK;
 }
@@ -38,7 +38,16 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
 // one tile of samples.
 MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
-    const lsp_options& o = ctx->opt;
+    lsp_options o = ctx->opt;
+    // AUTO with an autotuned entry for this size: take its mode, F and split
+    if (o.sincos_mode == LSP_SINCOS_AUTO && o.phase_mode == LSP_PHASE_FIXED64 && o.freqs_per_thread == 0 &&
+        o.split == 0) {
+        if (const TuneEntry* te = tuned(ctx, N, N_f)) {
+            o.sincos_mode = te->sincos;
+            o.freqs_per_thread = te->F;
+            o.split = (int)std::min<int64_t>(te->split, std::max<int64_t>(1, N / lsp::kTile));
+        }
+    }
     // Strip lengths measured best on GB300 for each mode (gapped_100k workload).
     if (o.phase_mode == LSP_PHASE_NAIVE_FP32) {
         s.mode = lsp::kModeNaive;
@@ -292,6 +301,7 @@ void lsp_destroy(lsp_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     if (ctx->done) cudaEventDestroy(ctx->done);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaGetLastError();
     delete ctx;
 }

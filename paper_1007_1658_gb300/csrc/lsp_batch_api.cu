@@ -22,54 +22,6 @@ void lsp::host::drop_plan(lsp_ctx* ctx) {
     ctx->plan = BatchPlan();
 }
 
-namespace {
-
-// Copy n elements of a host or device array into a host vector (ordered on
-// the context's stream, then waited for).
-template <class T>
-lsp_status fetch(lsp_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
-    dst.resize(n);
-    if (n == 0) return LSP_OK;
-    if (is_device_ptr(src)) {
-        LSP_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
-        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    } else {
-        std::memcpy(dst.data(), src, n * sizeof(T));
-    }
-    return LSP_OK;
-}
-
-lsp_status ensure_pinned(lsp_ctx* ctx, size_t bytes) {
-    if (bytes <= ctx->pinned_cap) return LSP_OK;
-    if (ctx->pinned) {
-        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        cudaFreeHost(ctx->pinned);
-        ctx->pinned = nullptr;
-        ctx->pinned_cap = 0;
-    }
-    const size_t want = bytes + bytes / 4 + 4096;
-    LSP_CUDA(ctx, cudaMallocHost(&ctx->pinned, want));
-    ctx->pinned_cap = want;
-    return LSP_OK;
-}
-
-// Device view of a caller array: the array itself if it is on the device,
-// else a context buffer filled from it (asynchronously, outside the graph).
-template <class T>
-lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf, const T** out) {
-    if (is_device_ptr(src)) {
-        *out = src;
-        return LSP_OK;
-    }
-    lsp_status st = ensure(ctx, buf, n * sizeof(T) + 16);
-    if (st != LSP_OK) return st;
-    if (n) LSP_CUDA(ctx, cudaMemcpyAsync(buf.p, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
-    *out = (const T*)buf.p;
-    return LSP_OK;
-}
-
-}  // namespace
-
 extern "C" {
 
 lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
@@ -188,34 +140,39 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         const int occ = lsp::batch_occupancy(mode, F);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
 
-        // capture the batch as one graph
+        // capture the batch as one graph, on a private stream (the caller's
+        // stream may be the legacy default stream, which cannot be captured);
+        // the graph is launched on the caller's stream below
+        if (!ctx->cap_stream) LSP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        LSP_CUDA(ctx, cudaStreamSynchronize(st));  // the work list copy must land before replays
         cudaGraph_t g = nullptr;
-        LSP_CUDA(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaMemsetAsync(ctx->b_head.p, 0, 16, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_maxkey.p, 0, n_out * 8, st);
+        const cudaStream_t cst = ctx->cap_stream;
+        LSP_CUDA(ctx, cudaStreamBeginCapture(cst, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemsetAsync(ctx->b_head.p, 0, 16, cst);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->b_maxkey.p, 0, n_out * 8, cst);
         if (e == cudaSuccess)
             e = lsp::launch_prep_stats(d_t, d_X, d_off, 0, n_curves, (lsp::CurveStats*)ctx->b_stats.p,
-                                       ctx->status_d, nullptr, nullptr, st);
+                                       ctx->status_d, nullptr, nullptr, cst);
         if (e == cudaSuccess) {
             const int64_t max_n = off[order[0] + 1] - off[order[0]];
             e = lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0,
                                          (const lsp::CurveStats*)ctx->b_stats.p, (uint4*)ctx->b_recA.p,
                                          (float4*)ctx->b_recB.p, nullptr, noise ? nullptr : (float*)ctx->b_xr.p,
-                                         st);
+                                         cst);
         }
         if (e == cudaSuccess && noise)
             e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
-                                       (float*)ctx->b_xr.p, st);
+                                       (float*)ctx->b_xr.p, cst);
         if (e == cudaSuccess && !items.empty())
             e = lsp::launch_batch(mode, F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
                                   (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves,
                                   (const uint4*)ctx->b_recA.p, (const float4*)ctx->b_recB.p,
                                   (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
-                                  (unsigned long long*)ctx->b_maxkey.p, st);
+                                  (unsigned long long*)ctx->b_maxkey.p, cst);
         if (e == cudaSuccess && (d_maxP || d_argmax))
             e = lsp::launch_unpack_max((const unsigned long long*)ctx->b_maxkey.p, (int64_t)n_out, d_maxP,
-                                       d_argmax, st);
-        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+                                       d_argmax, cst);
+        cudaError_t e2 = cudaStreamEndCapture(cst, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&pl.exec, g, 0);
         if (g) cudaGraphDestroy(g);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdarg>
+#include <cstring>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -33,6 +34,22 @@ struct BatchPlan {
     int kernels = 0;
 };
 
+// One autotuned choice for a (log2 N_t, log2 N_f) size bucket.
+struct TuneEntry {
+    int nt_bucket, nf_bucket;
+    int sincos, F, split;
+    float ms;
+};
+
+// State of the false-alarm surrogate's network (lsp_fap_*).
+struct FapState {
+    bool ready = false;
+    int H = 0;
+    int64_t n_params = 0;
+    int64_t step = 0;
+    DevBuf params, grad, m, v, mu_sig, ws, act, X, cnt, y, loss, q, rows, W, W_off, nw, counts;
+};
+
 }  // namespace host
 }  // namespace lsp
 
@@ -40,6 +57,7 @@ struct lsp_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream that batch graphs are captured on
     lsp_options opt{};
     std::string err;
     int sms = 0;
@@ -51,6 +69,8 @@ struct lsp_ctx {
     void* pinned = nullptr;  // host staging for the work list and small values
     size_t pinned_cap = 0;
     lsp::host::BatchPlan plan;
+    lsp::host::FapState fap;
+    std::vector<lsp::host::TuneEntry> tune;  // lsp_autotune results, used by AUTO
     int* status_d = nullptr;  // device status word (OR of kStatus* bits)
     int* status_h = nullptr;  // pinned mirror
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -142,8 +162,55 @@ inline bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Copy n elements of a host or device array into a host vector (ordered on
+// the context's stream, then waited for).
+template <class T>
+inline lsp_status fetch(lsp_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
+    dst.resize(n);
+    if (n == 0) return LSP_OK;
+    if (is_device_ptr(src)) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::memcpy(dst.data(), src, n * sizeof(T));
+    }
+    return LSP_OK;
+}
+
+inline lsp_status ensure_pinned(lsp_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->pinned_cap) return LSP_OK;
+    if (ctx->pinned) {
+        LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFreeHost(ctx->pinned);
+        ctx->pinned = nullptr;
+        ctx->pinned_cap = 0;
+    }
+    const size_t want = bytes + bytes / 4 + 4096;
+    LSP_CUDA(ctx, cudaMallocHost(&ctx->pinned, want));
+    ctx->pinned_cap = want;
+    return LSP_OK;
+}
+
+// Device view of a caller array: the array itself if it is on the device,
+// else a context buffer filled from it (asynchronously, outside the graph).
+template <class T>
+inline lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf, const T** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return LSP_OK;
+    }
+    lsp_status st = ensure(ctx, buf, n * sizeof(T) + 16);
+    if (st != LSP_OK) return st;
+    if (n) LSP_CUDA(ctx, cudaMemcpyAsync(buf.p, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    *out = (const T*)buf.p;
+    return LSP_OK;
+}
+
 // Launch shape of the single-curve path for the context's options.
 lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
+
+// Autotuned entry for this size bucket, or null.
+const TuneEntry* tuned(const lsp_ctx* ctx, int64_t N, int64_t N_f);
 
 // Release the cached batch graph.
 void drop_plan(lsp_ctx* ctx);

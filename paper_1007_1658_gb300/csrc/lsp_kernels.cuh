@@ -115,4 +115,30 @@ cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64
 cudaError_t launch_noise_prep(const int64_t* off, int n_curves, int n_real, const uint64_t* seed_dev,
                               int64_t total, float* xr, cudaStream_t st);
 
+// ---- false-alarm surrogate (features.cu, mlp.cu) ----
+
+// Spectral window of each pattern on its own window grid (persistent items).
+cudaError_t launch_window(int F, int grid, const BatchItem* items, int n_items, unsigned* head, const int64_t* off,
+                          const int64_t* nw, const uint4* recA, const float4* recB, float* W, const int64_t* W_off,
+                          cudaStream_t st);
+int window_occupancy(int F);
+// Dynamic shared memory of the features kernel for patterns of up to max_n samples.
+size_t features_smem_bytes(int64_t max_n);
+cudaError_t launch_features(int n_patterns, int64_t max_n, const double* t, const int64_t* off, const double* f0,
+                            const double* df, const int64_t* nf, const float* W, const int64_t* W_off,
+                            const int64_t* nw, float* feat, int* status, cudaStream_t st);
+
+int64_t mlp_param_count(int H);
+cudaError_t mlp_init(int H, uint64_t seed, float* params, cudaStream_t st);
+cudaError_t mlp_feature_stats(int n, const float* feat, float* mu, float* sig, cudaStream_t st);
+cudaError_t mlp_gather(int Bn, const int32_t* rows, int n_pat, const float* feat, const float* counts, const float* y,
+                       const float* mu, const float* sig, float* X, float* cnt, float* yy, cudaStream_t st);
+size_t mlp_workspace_floats(int H, int Bn);
+size_t mlp_act_bytes(int H, int Bn, bool fp32);
+cudaError_t mlp_forward_backward(int H, int Bn, bool fp32, const float* params, const float* X, const float* cnt,
+                                 const float* y, float* q, float* grad, float* loss, float* ws, void* act,
+                                 cudaStream_t st);
+cudaError_t mlp_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float c1,
+                     float c2, float eps, cudaStream_t st);
+
 }  // namespace lsp

@@ -39,7 +39,7 @@ class LspError(RuntimeError):
 class lsp_options(ctypes.Structure):
     _fields_ = [("sincos_mode", ctypes.c_int32), ("phase_mode", ctypes.c_int32),
                 ("freqs_per_thread", ctypes.c_int32), ("split", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("timing", ctypes.c_int32), ("mlp_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 def load():
@@ -84,6 +84,23 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_batch"):
         lib.lsp_batch.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
         lib.lsp_batch.restype = ctypes.c_int
+    if hasattr(lib, "lsp_fap_features"):
+        lib.lsp_fap_features.argtypes = [p, i32, p, p, p, p, p, p]
+        lib.lsp_fap_init.argtypes = [p, i32, u64, i32, p]
+        lib.lsp_fap_train_step.argtypes = [p, i32, p, i32, p, p, p, ctypes.c_float, p]
+        lib.lsp_fap_gradients.argtypes = [p, i32, p, p, p, p, p]
+        lib.lsp_fap_eval.argtypes = [p, i32, p, p, p]
+        lib.lsp_fap_predict.argtypes = [p, i32, p, p, p, p, p, p]
+        lib.lsp_fap_get_params.argtypes = [p, p, i64, ctypes.POINTER(ctypes.c_int64)]
+        lib.lsp_fap_set_params.argtypes = [p, i32, p, i64]
+        lib.lsp_fap_save.argtypes = [p, ctypes.c_char_p]
+        lib.lsp_fap_load.argtypes = [p, ctypes.c_char_p]
+        for name in ("lsp_fap_features", "lsp_fap_init", "lsp_fap_train_step", "lsp_fap_gradients", "lsp_fap_eval",
+                     "lsp_fap_predict", "lsp_fap_get_params", "lsp_fap_set_params", "lsp_fap_save", "lsp_fap_load"):
+            getattr(lib, name).restype = ctypes.c_int
+    if hasattr(lib, "lsp_autotune"):
+        lib.lsp_autotune.argtypes = [p, i64, i64, ctypes.POINTER(lsp_options)]
+        lib.lsp_autotune.restype = ctypes.c_int
     if hasattr(lib, "lsp_noise"):
         lib.lsp_noise.argtypes = [p, u64, i32, i32, i64, p]
         lib.lsp_noise.restype = ctypes.c_int
@@ -95,6 +112,14 @@ def options(**kw) -> lsp_options:
     for k, v in kw.items():
         setattr(o, k, int(v))
     return o
+
+
+def _like(ref, shape, dtype):
+    """An output array on the same side (device tensor / numpy) as `ref`."""
+    if hasattr(ref, "data_ptr"):
+        import torch
+        return torch.empty(shape, dtype={np.float32: torch.float32, np.int32: torch.int32}[dtype], device=ref.device)
+    return np.empty(shape, dtype=dtype)
 
 
 def _ptr(a):
@@ -133,13 +158,15 @@ class Context:
             try:
                 import torch
                 if torch.cuda.is_available():
-                    return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+                    s = torch.cuda.current_stream(self.device)
             except Exception:
-                pass
-            return None
-        if hasattr(s, "cuda_stream"):
-            return ctypes.c_void_p(s.cuda_stream)
-        return ctypes.c_void_p(int(s))
+                s = None
+            if s is None:
+                return None
+        h = s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+        # handle 0 is the legacy default stream; pass it as cudaStreamLegacy
+        # (0x1) because a NULL stream means "the context's own stream"
+        return ctypes.c_void_p(h if h else 1)
 
     def _check(self, st):
         if st != OK:
@@ -195,6 +222,79 @@ class Context:
         self._check(self._lib.lsp_noise(self.h, ctypes.c_uint64(int(seed)), int(curve), int(real), int(n), _ptr(out)))
         return out
 
+    def autotune(self, n_t, n_f):
+        """lsp_autotune: returns the chosen options as a dict."""
+        o = lsp_options()
+        self._bind_stream()
+        self._check(self._lib.lsp_autotune(self.h, int(n_t), int(n_f), ctypes.byref(o)))
+        return {"sincos_mode": o.sincos_mode, "freqs_per_thread": o.freqs_per_thread, "split": o.split}
+
+    # ---- learned false-alarm surrogate ----
+    def fap_features(self, t_off, t, f0, df, nf, out=None):
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        if out is None:
+            out = _like(t, (n, 32), np.float32)
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_features(self.h, n, _ptr(t_off), _ptr(t), _ptr(f0), _ptr(df), _ptr(nf),
+                                               _ptr(out)))
+        return out
+
+    def fap_init(self, features, hidden=256, seed=0):
+        n = int(features.shape[0])
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_init(self.h, int(hidden), ctypes.c_uint64(int(seed)), n, _ptr(features)))
+
+    def fap_train_step(self, rows, features, counts, targets, lr, loss_out=None):
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_train_step(self.h, int(rows.numel()), _ptr(rows), int(features.shape[0]),
+                                                 _ptr(features), _ptr(counts), _ptr(targets), float(lr),
+                                                 _ptr(loss_out)))
+
+    def fap_gradients(self, features, counts, targets):
+        B = int(features.shape[0])
+        n = ctypes.c_int64()
+        self._check(self._lib.lsp_fap_get_params(self.h, None, 0, ctypes.byref(n)))
+        g = np.empty(int(n.value) - 64, dtype=np.float32)
+        loss = np.empty(1, dtype=np.float32)
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_gradients(self.h, B, _ptr(features), _ptr(counts), _ptr(targets), _ptr(g),
+                                                _ptr(loss)))
+        return g, float(loss[0])
+
+    def fap_eval(self, features, counts, out=None):
+        B = int(features.shape[0])
+        if out is None:
+            out = _like(features, (B, 9), np.float32)
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_eval(self.h, B, _ptr(features), _ptr(counts), _ptr(out)))
+        return out
+
+    def fap_predict(self, t_off, t, f0, df, nf, out=None):
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        if out is None:
+            out = _like(t, (n, 9), np.float32)
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_predict(self.h, n, _ptr(t_off), _ptr(t), _ptr(f0), _ptr(df), _ptr(nf),
+                                              _ptr(out)))
+        return out
+
+    def fap_get_params(self):
+        n = ctypes.c_int64()
+        self._check(self._lib.lsp_fap_get_params(self.h, None, 0, ctypes.byref(n)))
+        out = np.empty(int(n.value), dtype=np.float32)
+        self._check(self._lib.lsp_fap_get_params(self.h, _ptr(out), out.size, ctypes.byref(n)))
+        return out
+
+    def fap_set_params(self, flat, hidden=256):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self._lib.lsp_fap_set_params(self.h, int(hidden), _ptr(flat), flat.size))
+
+    def fap_save(self, path):
+        self._check(self._lib.lsp_fap_save(self.h, str(path).encode()))
+
+    def fap_load(self, path):
+        self._check(self._lib.lsp_fap_load(self.h, str(path).encode()))
+
     def sync(self, timeout_s: float = -1.0):
         self._check(self._lib.lsp_sync(self.h, float(timeout_s)))
 
@@ -234,6 +334,7 @@ def periodogram_noalloc(t, X, f0, df, nf, out, stream=None):
         raw = torch.cuda.current_stream().cuda_stream
     else:
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    raw = raw if raw else 1  # the legacy default stream
     st = lib.lsp_periodogram_noalloc(_ptr(t), _ptr(X), int(t.numel()), float(f0), float(df), int(nf), _ptr(out),
                                      ctypes.c_void_p(raw))
     if st != OK:

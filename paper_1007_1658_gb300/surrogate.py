@@ -1,0 +1,174 @@
+"""Training and Monte-Carlo evaluation of the learned false-alarm surrogate.
+
+Orchestration only: the noise, the periodograms, their maxima, the pattern
+features and the network's forward, backward and Adam steps all run in
+liblsp.so's kernels (lsp_batch, lsp_fap_*); this module draws sampling
+patterns (synth.noise_batch), hands arrays to the C ABI and loops.
+
+  python -m paper_1007_1658_gb300.surrogate [--quick] [--out model.lspfap]
+
+trains on noise periodograms the batched engine generates and judges the
+trained network against brute-force Monte Carlo on held-out patterns,
+printing one JSON report.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import lsp, synth
+
+LEVELS = np.array([0.05, 0.10, 0.25, 0.50, 0.75, 0.90, 0.95, 0.98, 0.99])
+DEFAULT_MODEL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fap_surrogate.lspfap")
+
+
+class DevicePatterns:
+    """A batch of sampling patterns resident on the GPU."""
+
+    def __init__(self, b: synth.Batch, device):
+        import torch
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.batch = b
+        self.n = b.n
+        self.t_off, self.t, self.f0, self.df, self.nf = d(b.t_off), d(b.t), d(b.f0), d(b.df), d(b.nf)
+        nt = np.diff(b.t_off).astype(np.float32)
+        self.counts = d(np.column_stack([nt, b.nf.astype(np.float32)]))
+        self.total = int(b.t_off[-1])
+
+
+def mc_maxima(ctx: lsp.Context, pats: DevicePatterns, n_real: int, seed: int, max_floats: float = 6e8):
+    """Largest noise peak of n_real noise realizations of every pattern:
+    a [n_real, n] float32 device tensor, realizations drawn in chunks whose
+    noise buffer stays under max_floats values."""
+    import torch
+    chunk = max(1, min(n_real, int(max_floats // max(1, pats.total))))
+    out = torch.empty((n_real, pats.n), dtype=torch.float32, device=pats.t.device)
+    arg = torch.empty((chunk, pats.n), dtype=torch.int32, device=pats.t.device)
+    r = 0
+    while r < n_real:
+        k = min(chunk, n_real - r)
+        ctx.batch(pats.t_off, pats.t, pats.f0, pats.df, pats.nf, seed=seed + r, n_real=k,
+                  maxP=out[r:r + k], argmax=arg[:k])
+        r += k
+    return out
+
+
+def train(ctx: lsp.Context, n_patterns=1 << 14, n_real=16, steps=3000, batch=4096, lr=2e-3, hidden=256,
+          seed=2024, log_every=250, verbose=True):
+    """Train the surrogate on n_patterns x n_real noise periodograms."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    t0 = time.perf_counter()
+    b = synth.noise_batch(n_curves=n_patterns, seed=seed)
+    pats = DevicePatterns(b, dev)
+    t_gen = time.perf_counter() - t0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    targets = mc_maxima(ctx, pats, n_real, seed=seed * 7919 + 1).reshape(-1).contiguous()
+    ev[1].record()
+    feats = ctx.fap_features(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
+    ctx.fap_init(feats, hidden=hidden, seed=seed)
+    rng = np.random.default_rng(seed)
+    n_rows = n_real * n_patterns
+    losses = torch.zeros(steps, dtype=torch.float32, device=dev)
+    rows_h = torch.empty(batch, dtype=torch.int32).pin_memory()
+    rows_d = torch.empty(batch, dtype=torch.int32, device=dev)
+    ev[2].record()
+    for s in range(steps):
+        rows_h.numpy()[:] = rng.integers(0, n_rows, batch, dtype=np.int32)
+        rows_d.copy_(rows_h, non_blocking=True)
+        # cosine decay to 5% of the initial rate
+        lr_s = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * s / steps)))
+        ctx.fap_train_step(rows_d, feats, pats.counts, targets, lr_s, loss_out=losses[s:s + 1])
+        if verbose and log_every and (s % log_every == 0 or s == steps - 1):
+            torch.cuda.synchronize(dev)
+            print("step %5d  loss %.4f  lr %.2e" % (s, float(losses[s]), lr_s), flush=True)
+    ev[3].record()
+    torch.cuda.synchronize(dev)
+    return {"patterns": n_patterns, "realizations": n_real, "periodograms": n_rows,
+            "terms": int(b.terms) * n_real, "steps": steps, "batch": batch,
+            "gpu_s_data": ev[0].elapsed_time(ev[1]) / 1e3, "gpu_s_train": ev[2].elapsed_time(ev[3]) / 1e3,
+            "cpu_s_patterns": t_gen, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+            "loss_tail_mean": float(losses[-min(200, steps):].mean())}
+
+
+def hidden_of(ctx: lsp.Context) -> int:
+    """Hidden width of the context's network, from its parameter count."""
+    n = ctx.fap_get_params().size - 64
+    # 32H + H + 2(H^2 + H) + 9H + 9 = 2H^2 + 44H + 9
+    return int(round((-44 + np.sqrt(44 * 44 - 8 * (9 - n))) / 4))
+
+
+def eq3_quantiles(n_t, n_f):
+    """Eq. 3's quantiles of the largest of N_f independent noise peaks."""
+    n_t = np.asarray(n_t, np.float64)[:, None]
+    n_f = np.asarray(n_f, np.float64)[:, None]
+    a = -np.expm1(np.log(LEVELS[None, :]) / n_f)
+    return 0.5 * n_t * (-np.expm1(2.0 / (n_t - 3.0) * np.log(a)))
+
+
+def judge(ctx: lsp.Context, n_patterns=256, n_real=10000, seed=777001):
+    """Held-out patterns: surrogate quantiles and Eq. 3's against brute-force
+    Monte Carlo with n_real noise realizations each; GPU seconds of both."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    b = synth.noise_batch(n_curves=n_patterns, seed=seed)
+    pats = DevicePatterns(b, dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ctx.fap_predict(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)  # warm-up
+    torch.cuda.synchronize(dev)
+    ev[0].record()
+    q_sur = ctx.fap_predict(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
+    ev[1].record()
+    maxP = mc_maxima(ctx, pats, n_real, seed=seed * 31 + 5)
+    ev[2].record()
+    torch.cuda.synchronize(dev)
+    q_sur = q_sur.cpu().numpy().astype(np.float64)
+    # the same weights evaluated with FP32 activations
+    ctx32 = lsp.Context(ctx.device, mlp_fp32=1)
+    ctx32.fap_set_params(ctx.fap_get_params(), hidden=hidden_of(ctx))
+    q32 = ctx32.fap_predict(pats.t_off, pats.t, pats.f0, pats.df, pats.nf).cpu().numpy().astype(np.float64)
+    ctx32.close()
+    m = np.sort(maxP.cpu().numpy().astype(np.float64), axis=0)
+    idx = np.minimum(n_real - 1, np.ceil(LEVELS * n_real).astype(int) - 1)   # empirical quantiles
+    q_mc = m[idx, :].T
+    q_eq3 = eq3_quantiles(np.diff(b.t_off), b.nf)
+    rel_sur = np.abs(q_sur - q_mc) / q_mc
+    rel_32 = np.abs(q32 - q_mc) / q_mc
+    rel_eq3 = np.abs(q_eq3 - q_mc) / q_mc
+    t_sur = ev[0].elapsed_time(ev[1]) / 1e3
+    t_mc = ev[1].elapsed_time(ev[2]) / 1e3
+    return {"patterns": n_patterns, "realizations": n_real, "levels": LEVELS.tolist(),
+            "mean_rel_err_surrogate": rel_sur.mean(axis=0).tolist(),
+            "p95_rel_err_surrogate": np.percentile(rel_sur, 95, axis=0).tolist(),
+            "mean_rel_err_surrogate_fp32_activations": rel_32.mean(axis=0).tolist(),
+            "mean_rel_err_eq3": rel_eq3.mean(axis=0).tolist(),
+            "max_level_mean_rel_err_surrogate": float(rel_sur.mean(axis=0).max()),
+            "max_level_mean_rel_err_eq3": float(rel_eq3.mean(axis=0).max()),
+            "gpu_s_surrogate": t_sur, "gpu_s_mc": t_mc, "gpu_s_ratio": t_mc / max(t_sur, 1e-9),
+            "mc_terms": int(b.terms) * n_real}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true", help="small run (minutes -> seconds)")
+    ap.add_argument("--out", default=DEFAULT_MODEL)
+    ap.add_argument("--steps", type=int, default=0)
+    args = ap.parse_args()
+    ctx = lsp.Context(0)
+    if args.quick:
+        tr = train(ctx, n_patterns=2048, n_real=8, steps=args.steps or 600, batch=2048, log_every=100)
+        jd = judge(ctx, n_patterns=64, n_real=2000)
+    else:
+        tr = train(ctx, steps=args.steps or 3000)
+        jd = judge(ctx)
+    ctx.fap_save(args.out)
+    print(json.dumps({"train": tr, "judge": jd, "model": os.path.basename(args.out)}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -231,3 +231,18 @@ def test_timing_and_launch_count(lsp):
     assert prep > 0 and main > 0 and fin >= 0
     assert ctx.last_launch_count() in (3, 4)
     ctx.close()
+
+
+def test_autotune_choice_is_used_and_accurate(lsp):
+    from paper_1007_1658_gb300 import synth
+    ctx = lsp.Context(0)
+    c = synth.plain_1k()
+    chosen = ctx.autotune(c.t.size, c.nf)
+    assert chosen["sincos_mode"] in (1, 2, 3) and chosen["freqs_per_thread"] in (8, 16, 24) and chosen["split"] >= 1
+    ref = oracle.periodogram(c.t, c.X, c.f0, c.df, c.nf)
+    got = _run(ctx, c.t, c.X, c.f0, c.df, c.nf)  # AUTO: takes the tuned entry
+    assert_parity(got, ref, what="autotuned plain_1k %s" % chosen)
+    g = synth.gapped_100k()
+    chosen = ctx.autotune(g.t.size, g.nf)
+    assert chosen["split"] >= 1
+    ctx.close()

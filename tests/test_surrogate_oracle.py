@@ -31,14 +31,18 @@ def test_gelu_is_x_times_normal_cdf_and_its_derivative():
     assert np.allclose(S.gelu_grad(x), fd, rtol=1e-7, atol=1e-9)
 
 
-def test_head_with_zero_network_is_eq3_times_powers_of_two():
-    # all weights zero: z = 0, o_1 = 0, o_l = (l-1) log 2, so q_l = q_l^Eq3 2^(l-1)
+def test_head_with_zero_output_is_eq3():
+    # an untrained network (zero output layer) predicts Eq. 3's quantiles exactly
     rng = np.random.default_rng(0)
-    ps = [np.zeros_like(p) for p in S.init_params(rng, hidden=4)]
+    ps = S.init_params(rng, hidden=4)
     counts = np.array([[300.0, 600.0], [5000.0, 10000.0]])
     q, _, _ = S.mlp_forward(ps, rng.normal(size=(2, S.N_FEATURES)), counts)
-    expect = S.eq3_quantile(counts[:, :1], counts[:, 1:], S.LEVELS[None, :]) * 2.0 ** np.arange(S.N_LEVELS)
+    expect = S.eq3_quantile(counts[:, :1], counts[:, 1:], S.LEVELS[None, :])
     assert np.allclose(q, expect, rtol=1e-12)
+    # and any output keeps the quantiles ordered
+    ps[6] = rng.normal(0, 3.0, ps[6].shape)
+    q, _, _ = S.mlp_forward(ps, rng.normal(size=(50, S.N_FEATURES)), np.tile(counts, (25, 1)))
+    assert np.all(np.diff(q, axis=1) > 0)
 
 
 def test_backward_matches_finite_differences():
