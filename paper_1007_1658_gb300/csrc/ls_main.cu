@@ -171,7 +171,9 @@ MainFn main_fn_f(int F) {
         case 4: return ls_main_kernel<4, MODE>;
         case 8: return ls_main_kernel<8, MODE>;
         case 16: return ls_main_kernel<16, MODE>;
+        case 20: return MODE == kMufu ? nullptr : ls_main_kernel<20, MODE>;
         case 24: return ls_main_kernel<24, MODE>;
+        case 28: return MODE == kMufu ? nullptr : ls_main_kernel<28, MODE>;
         default: return nullptr;
     }
 }

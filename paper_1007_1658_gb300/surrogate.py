@@ -57,43 +57,64 @@ def mc_maxima(ctx: lsp.Context, pats: DevicePatterns, n_real: int, seed: int, ma
     return out
 
 
-def train(ctx: lsp.Context, n_patterns=1 << 14, n_real=16, steps=3000, batch=4096, lr=2e-3, hidden=256,
-          seed=2024, log_every=250, verbose=True):
-    """Train the surrogate on n_patterns x n_real noise periodograms."""
+def _pinball(q, y):
+    """Mean pinball loss of quantiles q [n, 9] against samples y [r, n] (host)."""
+    u = y[:, :, None] - q[None, :, :]
+    return float(np.mean(np.sum(np.maximum(LEVELS * u, (LEVELS - 1.0) * u), axis=2)))
+
+
+def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=2000, batch=4096, lr=1e-3, hidden=256,
+          seed=2024, n_val=2048, eval_every=100, verbose=True):
+    """Train the surrogate on n_patterns x n_real noise periodograms, keeping
+    the weights with the lowest pinball loss on n_val validation patterns."""
     import torch
     dev = torch.device("cuda", ctx.device)
     t0 = time.perf_counter()
     b = synth.noise_batch(n_curves=n_patterns, seed=seed)
+    vb = synth.noise_batch(n_curves=n_val, seed=seed + 1)
     pats = DevicePatterns(b, dev)
+    vpats = DevicePatterns(vb, dev)
     t_gen = time.perf_counter() - t0
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record()
     targets = mc_maxima(ctx, pats, n_real, seed=seed * 7919 + 1).reshape(-1).contiguous()
     ev[1].record()
+    vtargets = mc_maxima(ctx, vpats, 8, seed=seed * 7919 + 2).cpu().numpy().astype(np.float64)
     feats = ctx.fap_features(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
+    vfeats = ctx.fap_features(vpats.t_off, vpats.t, vpats.f0, vpats.df, vpats.nf)
     ctx.fap_init(feats, hidden=hidden, seed=seed)
+    val = lambda: _pinball(ctx.fap_eval(vfeats, vpats.counts).cpu().numpy().astype(np.float64), vtargets)
+    best_loss, best_step, best_params = val(), 0, ctx.fap_get_params()
+    val_eq3 = best_loss
     rng = np.random.default_rng(seed)
     n_rows = n_real * n_patterns
     losses = torch.zeros(steps, dtype=torch.float32, device=dev)
-    rows_h = torch.empty(batch, dtype=torch.int32).pin_memory()
     rows_d = torch.empty(batch, dtype=torch.int32, device=dev)
-    ev[2].record()
+    history = []
+    gpu_s_train = 0.0
     for s in range(steps):
-        rows_h.numpy()[:] = rng.integers(0, n_rows, batch, dtype=np.int32)
-        rows_d.copy_(rows_h, non_blocking=True)
+        rows_d.copy_(torch.from_numpy(rng.integers(0, n_rows, batch, dtype=np.int32)))
         # cosine decay to 5% of the initial rate
         lr_s = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * s / steps)))
+        ev[2].record()
         ctx.fap_train_step(rows_d, feats, pats.counts, targets, lr_s, loss_out=losses[s:s + 1])
-        if verbose and log_every and (s % log_every == 0 or s == steps - 1):
-            torch.cuda.synchronize(dev)
-            print("step %5d  loss %.4f  lr %.2e" % (s, float(losses[s]), lr_s), flush=True)
-    ev[3].record()
-    torch.cuda.synchronize(dev)
+        ev[3].record()
+        ev[3].synchronize()
+        gpu_s_train += ev[2].elapsed_time(ev[3]) / 1e3
+        if eval_every and (s % eval_every == eval_every - 1 or s == steps - 1):
+            v = val()
+            history.append((s + 1, round(v, 5)))
+            if v < best_loss:
+                best_loss, best_step, best_params = v, s + 1, ctx.fap_get_params()
+            if verbose:
+                print("step %5d  train %.4f  val %.4f  best %.4f@%d" % (s + 1, float(losses[s]), v, best_loss,
+                                                                      best_step), flush=True)
+    ctx.fap_set_params(best_params, hidden=hidden)
     return {"patterns": n_patterns, "realizations": n_real, "periodograms": n_rows,
-            "terms": int(b.terms) * n_real, "steps": steps, "batch": batch,
-            "gpu_s_data": ev[0].elapsed_time(ev[1]) / 1e3, "gpu_s_train": ev[2].elapsed_time(ev[3]) / 1e3,
-            "cpu_s_patterns": t_gen, "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
-            "loss_tail_mean": float(losses[-min(200, steps):].mean())}
+            "terms": int(b.terms) * n_real, "steps": steps, "batch": batch, "lr": lr,
+            "gpu_s_data": ev[0].elapsed_time(ev[1]) / 1e3, "gpu_s_train": gpu_s_train,
+            "cpu_s_patterns": t_gen, "val_loss_eq3": val_eq3, "val_loss_best": best_loss, "best_step": best_step,
+            "val_history": history}
 
 
 def hidden_of(ctx: lsp.Context) -> int:
@@ -161,10 +182,10 @@ def main():
     args = ap.parse_args()
     ctx = lsp.Context(0)
     if args.quick:
-        tr = train(ctx, n_patterns=2048, n_real=8, steps=args.steps or 600, batch=2048, log_every=100)
+        tr = train(ctx, n_patterns=4096, n_real=4, steps=args.steps or 400, batch=2048, n_val=512, eval_every=100)
         jd = judge(ctx, n_patterns=64, n_real=2000)
     else:
-        tr = train(ctx, steps=args.steps or 3000)
+        tr = train(ctx, steps=args.steps or 2000)
         jd = judge(ctx)
     ctx.fap_save(args.out)
     print(json.dumps({"train": tr, "judge": jd, "model": os.path.basename(args.out)}), flush=True)

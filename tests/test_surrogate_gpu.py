@@ -180,3 +180,29 @@ def test_untrained_context_reports_no_model(lsp):
         ctx.fap_eval(feat, counts)
     assert e.value.status == lsp.ERR_NO_MODEL
     ctx.close()
+
+
+def test_committed_model_beats_eq3_against_monte_carlo(lsp):
+    """What the trained network gains over the method without it: on held-out
+    patterns, its max-peak quantiles are closer to brute-force Monte Carlo than
+    Eq. 3's (exponent N_f), and within 5% at every level."""
+    from paper_1007_1658_gb300 import surrogate as SU
+    ctx = lsp.Context(0)
+    ctx.fap_load(SU.DEFAULT_MODEL)
+    jd = SU.judge(ctx, n_patterns=48, n_real=3000, seed=424242)
+    sur = np.array(jd["mean_rel_err_surrogate"])
+    eq3 = np.array(jd["mean_rel_err_eq3"])
+    assert sur.max() <= 0.05, sur
+    assert sur.max() < eq3.max() and sur.mean() < eq3.mean(), (sur, eq3)
+    assert jd["gpu_s_ratio"] >= 100.0
+    ctx.close()
+
+
+def test_quick_training_improves_on_eq3(lsp):
+    """Training from scratch on engine-generated noise periodograms lowers the
+    validation pinball loss below Eq. 3's (the untrained network's)."""
+    from paper_1007_1658_gb300 import surrogate as SU
+    ctx = lsp.Context(0)
+    tr = SU.train(ctx, n_patterns=2048, n_real=4, steps=150, batch=2048, n_val=256, eval_every=50, verbose=False)
+    assert tr["val_loss_best"] < tr["val_loss_eq3"]
+    ctx.close()
