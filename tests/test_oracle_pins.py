@@ -238,3 +238,21 @@ def test_noise_is_standard_normal_and_stream_separated():
     assert abs(np.corrcoef(x, y)[0, 1]) < 0.03 and abs(np.corrcoef(x, z)[0, 1]) < 0.03
     # a prefix is the same stream
     assert np.array_equal(oracle.noise(2024, 3, 0, 13), x[:13])
+
+
+def test_even_grid_noise_maxima_follow_the_dirichlet_law():
+    # N even, interior Fourier frequencies: the normalized peak heights 2P_k/N are
+    # the first N/2 - 1 components of a Dirichlet(1, ..., 1, 1/2) vector (the
+    # mean-removed noise splits into orthogonal cos/sin planes plus the Nyquist
+    # cosine); the oracle's noise maxima must follow its maximum.
+    N, R = 64, 2500
+    t = np.arange(N, dtype=float)
+    nf = N // 2 - 1
+    fr = np.arange(1, nf + 1) / N
+    rng = np.random.default_rng(12)
+    m = np.array([oracle.periodogram_at(t, rng.normal(size=N), fr).max() for _ in range(R)])
+    g = np.concatenate([rng.gamma(1.0, size=(R, nf)), rng.gamma(0.5, size=(R, 1))], axis=1)
+    exact = N / 2 * (g[:, :nf].max(axis=1) / g.sum(axis=1))
+    assert stats.ks_2samp(m, exact).pvalue > 1e-3
+    # the single-peak marginal of the same law is Eq. 3's Beta(1, (N-3)/2)
+    assert stats.kstest(g[:, 0] / g.sum(axis=1), stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
