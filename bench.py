@@ -115,7 +115,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -124,6 +124,7 @@ class ClockSampler:
             try:
                 sm.append(float(f[1]))
                 mx.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 continue
             for n, v in zip(names, f[5:9]):
@@ -132,7 +133,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": float(np.median(pw)) if pw else None}
 
 
 def cpu_baseline_sample(c, n_bins: int):
@@ -304,7 +305,7 @@ def run_batch_bench(ctx, torch, dev, stream, args):
     arg = torch.empty(b.n, dtype=torch.int32, device=dev)
     bctx = lsp.Context(dev.index or 0, stream=stream)
     seed = 1234
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), ClockSampler(dev.index or 0) as clk:
         for _ in range(2):
             bctx.batch(off, t, f0, df, nf, seed=seed, maxP=maxP, argmax=arg)
         bctx.sync(300.0)
@@ -357,7 +358,7 @@ def run_batch_bench(ctx, torch, dev, stream, args):
             "terms_per_s": b.terms / (batch_ms * 1e-3), "plain_ms": plain_ms,
             "plain_curves_per_s": b.n / (plain_ms * 1e-3), "plain_terms_per_s": b.terms / (plain_ms * 1e-3),
             "plain_launches": launches, "batch_launches": 1, "speedup_vs_plain": plain_ms / batch_ms,
-            "max_rel_diff_batch_vs_plain": agree}
+            "max_rel_diff_batch_vs_plain": agree, "clocks": clk.summary()}
 
 
 def main():

@@ -75,7 +75,9 @@ typedef struct lsp_options {
     int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */
-    int32_t reserved[6];      /* must be zero                                          */
+    int32_t batch_rhs;        /* lsp_batch with n_real > 1: realizations sharing one pass
+                                 over the samples (0 = auto, 1 = one at a time, 2|4|8)  */
+    int32_t reserved[5];      /* must be zero                                          */
 } lsp_options;
 
 /* Fill *opt with the defaults (AUTO sin/cos, FIXED64 phase, automatic launch shape). */
@@ -134,6 +136,12 @@ lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64
  * maxP_out, argmax_out (optional, [n_real * n_curves], index r * n_curves + c):
  *   the largest P of each periodogram and its bin k (lowest k on ties; -1 and
  *   0 for a curve with N_f = 0).
+ * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 4)
+ * share each pass over a curve's samples: the phase, the sin/cos recurrence
+ * and CC, CS are computed once for the group and only XC, XS per realization
+ * (strips of 8, 8, 4 frequencies for R = 2, 4, 8), which halves the
+ * arithmetic per periodogram; each (frequency, realization) is computed
+ * exactly as the one-at-a-time kernel with the same strip length would.
  * At least one output must be given.  Arrays may be host or device pointers
  * (metadata is read on the host in either case); the sin/cos mode and strip
  * length follow the context's options (the naive FP32 phase is not offered).

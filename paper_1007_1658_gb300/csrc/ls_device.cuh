@@ -136,22 +136,93 @@ struct Strip {
     }
 };
 
+// Multi-right-hand-side strip: R realizations of one sampling pattern share
+// the phase, the sin/cos recurrence and the CC, CS sums; each keeps its own
+// XC, XS.  Per term and realization: 2 FFMA plus (2 recurrence + 2 CC/CS)/R,
+// instead of 6.  The arithmetic of every (frequency, realization) pair is the
+// single-realization strip's, in the same order, so results are identical.
+template <int F, int R, int MODE>
+struct MStrip {
+    float xc[F][R], xs[F][R], cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
+            cc[i] = cs[i] = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) xc[i][r] = xs[i][r] = 0.f;
+        }
+    }
+
+    __device__ __forceinline__ void acc(int i, const float (&x)[R], float c, float s) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xc[i][r] = fmaf(x[r], c, xc[i][r]);
+            xs[i][r] = fmaf(x[r], s, xs[i][r]);
+        }
+        cc[i] = fmaf(c, c, cc[i]);
+        cs[i] = fmaf(c, s, cs[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], uint32_t k0) {
+        uint32_t p = top_phase(A, k0);
+        if (MODE == kMufu) {
+            const uint32_t du = __float_as_uint(B.w);
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float s, c;
+                __sincosf(phase_to_angle(p), &s, &c);
+                acc(i, x, c, s);
+                p += du;
+            }
+        } else {
+            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            float s, c;
+            __sincosf(phase_to_angle(p), &s, &c);
+            float cp = c, sp = s;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                acc(i, x, c, s);
+                if (i + 1 < F) {
+                    float cn, sn;
+                    if (MODE == kRecur || i == 0) {
+                        cn = fmaf(c, C, -s * S);
+                        sn = fmaf(s, C, c * S);
+                    } else {
+                        cn = fmaf(C2, c, -cp);
+                        sn = fmaf(C2, s, -sp);
+                    }
+                    cp = c;
+                    sp = s;
+                    c = cn;
+                    s = sn;
+                }
+            }
+        }
+    }
+};
+
 // Double-buffered cp.async pipeline over the samples [j0, j1) in tiles of
 // kTile: stages the two 16-byte phase records of every sample and, when
 // `xr` is given, the sample values from that array; calls
 // body(a, b, x_or_null, n) once per tile with the tile in shared memory.
 // Every thread of the CTA must call it (it synchronizes the CTA).
-template <bool XARR>
-struct TileSmem {
+// NX rows of x values may come along: row r of a tile is xr[r * xstride + j].
+template <int NX>
+struct TileSmemN {
     uint4 A[2][kTile];
     float4 B[2][kTile];
-    float X[2][XARR ? kTile : 1];
+    float X[2][NX > 0 ? NX : 1][NX > 0 ? kTile : 1];
 };
 
-template <bool XARR, class Body>
-__device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* __restrict__ recA,
-                                              const float4* __restrict__ recB, const float* __restrict__ xr,
-                                              int64_t j0, int64_t j1, Body&& body) {
+template <bool XARR>
+using TileSmem = TileSmemN<XARR ? 1 : 0>;
+
+template <int NX, class Body>
+__device__ __forceinline__ void for_each_tile_n(TileSmemN<NX>& sm, const uint4* __restrict__ recA,
+                                                const float4* __restrict__ recB, const float* __restrict__ xr,
+                                                int64_t xstride, int nx_valid, int64_t j0, int64_t j1,
+                                                Body&& body) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ntiles = j1 > j0 ? (int)((j1 - j0 + kTile - 1) / kTile) : 0;
     auto stage = [&](int buf, int64_t jt) {
@@ -159,7 +230,13 @@ __device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* _
         for (int q = tid; q < n; q += nt) {
             cp_async16(&sm.A[buf][q], recA + jt + q);
             cp_async16(&sm.B[buf][q], recB + jt + q);
-            if (XARR) cp_async4(&sm.X[buf][q], xr + jt + q);
+#pragma unroll
+            for (int r = 0; r < NX; ++r) {
+                if (r < nx_valid)
+                    cp_async4(&sm.X[buf][r][q], xr + (size_t)r * (size_t)xstride + jt + q);
+                else
+                    sm.X[buf][r][q] = 0.f;  // missing realizations of the last group add nothing
+            }
         }
     };
     if (ntiles > 0) stage(0, j0);
@@ -171,9 +248,19 @@ __device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* _
         cp_async_wait1();
         __syncthreads();
         const int n = (int)min((int64_t)kTile, j1 - jt);
-        body(sm.A[it & 1], sm.B[it & 1], XARR ? sm.X[it & 1] : nullptr, n);
+        body(sm.A[it & 1], sm.B[it & 1], sm.X[it & 1], n);
         __syncthreads();
     }
+}
+
+template <bool XARR, class Body>
+__device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* __restrict__ recA,
+                                              const float4* __restrict__ recB, const float* __restrict__ xr,
+                                              int64_t j0, int64_t j1, Body&& body) {
+    for_each_tile_n<XARR ? 1 : 0>(sm, recA, recB, xr, 0, XARR ? 1 : 0, j0, j1,
+                                  [&](const uint4* a, const float4* b, const float (*x)[XARR ? kTile : 1], int n) {
+                                      body(a, b, XARR ? x[0] : nullptr, n);
+                                  });
 }
 
 }  // namespace dev

@@ -28,7 +28,9 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
     if ((F == 20 || F == 28) && (o->sincos_mode == LSP_SINCOS_MUFU || o->phase_mode == LSP_PHASE_NAIVE_FP32))
         return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread 20 and 28 are recurrence-only");
     if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");
-    for (int i = 0; i < 6; ++i)
+    if (o->batch_rhs != 0 && o->batch_rhs != 1 && o->batch_rhs != 2 && o->batch_rhs != 4 && o->batch_rhs != 8)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "batch_rhs must be 0, 1, 2, 4 or 8");
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "reserved option fields must be zero");
     return LSP_OK;
 }

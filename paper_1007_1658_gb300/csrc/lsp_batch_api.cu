@@ -70,7 +70,14 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
     const MainShape shape = choose_shape(ctx, 2 * lsp::kTile, 1);
     if (shape.mode == lsp::kModeNaive)
         return fail(ctx, LSP_ERR_UNSUPPORTED, "lsp_batch does not offer the naive FP32 phase");
-    const int mode = shape.mode, F = shape.F;
+    const int mode = shape.mode;
+    // realizations per pass over the samples (multi-RHS) and the strip length that goes with it
+    int R = 1;
+    if (n_real > 1) {
+        R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : 4;
+        if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
+    }
+    const int F = R == 1 ? shape.F : (R == 8 ? 4 : 8);
     const int64_t per_block = lsp::freqs_per_block(F);
 
     // ---- device views of the inputs (host arrays are copied in, outside the graph) ----
@@ -109,8 +116,8 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
                                            ctx->b_head.p, ctx->b_seed.p, ctx->b_maxkey.p, ctx->b_items.p};
     BatchPlan& pl = ctx->plan;
     const bool same = pl.valid && pl.n_curves == n_curves && pl.n_real == n_real && pl.mode == mode &&
-                      pl.F == F && pl.noise == noise && pl.ptrs == ptrs && pl.t_off == off && pl.nf == nf &&
-                      pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
+                      pl.F == F && pl.R == R && pl.noise == noise && pl.ptrs == ptrs && pl.t_off == off &&
+                      pl.nf == nf && pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
     if (!same) {
         drop_plan(ctx);
         // work list: curves longest first (each item costs ~N_t), then blocks, then realizations
@@ -122,7 +129,7 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         for (int c : order) {
             const int64_t nfb = (nf[c] + per_block - 1) / per_block;
             for (int64_t fb = 0; fb < nfb; ++fb)
-                for (int r = 0; r < n_real; ++r) items.push_back({c, r, (int32_t)fb, 0});
+                for (int r = 0; r < n_real; r += R) items.push_back({c, r, (int32_t)fb, std::min(R, n_real - r)});
         }
         if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
         const size_t item_bytes = items.size() * sizeof(lsp::BatchItem);
@@ -137,7 +144,8 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         std::vector<const void*> ptrs2 = ptrs;
         ptrs2.back() = ctx->b_items.p;
         (void)old_items;
-        const int occ = lsp::batch_occupancy(mode, F);
+        const bool xrec = n_real == 1;  // x travels inside the sample records
+        const int occ = R > 1 ? lsp::mrhs_occupancy(mode, F, R) : lsp::batch_occupancy(mode, F, xrec);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
 
         // capture the batch as one graph, on a private stream (the caller's
@@ -162,9 +170,14 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         }
         if (e == cudaSuccess && noise)
             e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
-                                       (float*)ctx->b_xr.p, cst);
-        if (e == cudaSuccess && !items.empty())
-            e = lsp::launch_batch(mode, F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+                                       (float*)ctx->b_xr.p, (float4*)ctx->b_recB.p, cst);
+        if (e == cudaSuccess && !items.empty() && R > 1)
+            e = lsp::launch_mrhs(mode, F, R, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+                                 (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves, (const uint4*)ctx->b_recA.p,
+                                 (const float4*)ctx->b_recB.p, (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
+                                 (unsigned long long*)ctx->b_maxkey.p, cst);
+        else if (e == cudaSuccess && !items.empty())
+            e = lsp::launch_batch(mode, F, xrec, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
                                   (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves,
                                   (const uint4*)ctx->b_recA.p, (const float4*)ctx->b_recB.p,
                                   (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
@@ -187,6 +200,7 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         pl.n_real = n_real;
         pl.mode = mode;
         pl.F = F;
+        pl.R = R;
         pl.noise = noise;
         pl.t_off = off;
         pl.nf = nf;

@@ -25,7 +25,7 @@ struct DevBuf {
 struct BatchPlan {
     bool valid = false;
     std::vector<const void*> ptrs;          // every pointer argument of the call
-    int n_curves = 0, n_real = 0, mode = 0, F = 0;
+    int n_curves = 0, n_real = 0, mode = 0, F = 0, R = 1;
     bool noise = false;
     std::vector<int64_t> t_off, nf, p_off;
     std::vector<double> f0, df;

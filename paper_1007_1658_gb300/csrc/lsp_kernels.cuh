@@ -91,17 +91,29 @@ cudaError_t launch_finalize(const MainShape& s, const float* part, int64_t N, in
 // frequencies of one realization of one curve.
 struct BatchItem {
     int32_t curve;
-    int32_t real;
+    int32_t real;    // realization (first of the group for multi-RHS items)
     int32_t fblock;
-    int32_t pad;
+    int32_t pad;     // multi-RHS items: realizations in the group
 };
 
-int batch_occupancy(int mode, int F);
+int batch_occupancy(int mode, int F, bool x_in_records);
 
-cudaError_t launch_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+// x_in_records: every item's x is the x field of recB (one realization);
+// otherwise realization r reads xr[r][*].
+cudaError_t launch_batch(int mode, int F, bool x_in_records, int grid, const BatchItem* items, int n_items,
+                         unsigned* head,
                          const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,
                          const float4* recB, const float* xr, float* P_out, const int64_t* P_off, int64_t P_total,
                          unsigned long long* maxkey, cudaStream_t st);
+
+// Multi-RHS batch: items carry a group of up to R realizations (real = first,
+// pad = count) sharing phases, recurrence and CC/CS; shapes (F, R) in
+// {(8, 4), (8, 2), (4, 8)}.
+int mrhs_occupancy(int mode, int F, int R);
+cudaError_t launch_mrhs(int mode, int F, int R, int grid, const BatchItem* items, int n_items, unsigned* head,
+                        const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,
+                        const float4* recB, const float* xr, float* P_out, const int64_t* P_off, int64_t P_total,
+                        unsigned long long* maxkey, cudaStream_t st);
 
 cudaError_t launch_unpack_max(const unsigned long long* maxkey, int64_t n, float* maxP, int32_t* argmax,
                               cudaStream_t st);
@@ -109,11 +121,12 @@ cudaError_t launch_unpack_max(const unsigned long long* maxkey, int64_t n, float
 // Raw N(0,1) values of (seed, curve, realization), samples 0..n-1.
 cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float* out, cudaStream_t st);
 
-// Normalized noise for every (curve, realization) into xr[real][total]; the
-// seed is read from device memory so a captured graph can be replayed with
-// a new seed.
+// Normalized noise for every (curve, realization) into xr[real][total] and,
+// with a single realization, also into the x field of the sample records
+// recB; the seed is read from device memory so a captured graph can be
+// replayed with a new seed.
 cudaError_t launch_noise_prep(const int64_t* off, int n_curves, int n_real, const uint64_t* seed_dev,
-                              int64_t total, float* xr, cudaStream_t st);
+                              int64_t total, float* xr, float4* recB, cudaStream_t st);
 
 // ---- false-alarm surrogate (features.cu, mlp.cu) ----
 

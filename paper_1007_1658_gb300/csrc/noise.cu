@@ -94,7 +94,7 @@ noise_raw_kernel(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float*
 // variance in FP64 over two passes.
 __global__ void __launch_bounds__(kNoiseThreads)
 noise_prep_kernel(const int64_t* __restrict__ off, const uint64_t* __restrict__ seed_p, int64_t total,
-                  float* __restrict__ xr) {
+                  float* __restrict__ xr, float4* __restrict__ recB) {
     __shared__ double sh[33];
     const int c = blockIdx.x, r = blockIdx.y;
     const int64_t b = off[c], n = off[c + 1] - off[c];
@@ -119,7 +119,11 @@ noise_prep_kernel(const int64_t* __restrict__ off, const uint64_t* __restrict__ 
     }
     const double var = block_sum(v, sh) / (double)n;
     const double inv_sd = var > 0.0 ? 1.0 / sqrt(var) : 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) x[j] = (float)(((double)x[j] - mean) * inv_sd);
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const float xh = (float)(((double)x[j] - mean) * inv_sd);
+        x[j] = xh;
+        if (recB) recB[b + j].x = xh;  // single realization: straight into the sample records
+    }
 }
 
 }  // namespace
@@ -134,9 +138,9 @@ cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64
 }
 
 cudaError_t launch_noise_prep(const int64_t* off, int n_curves, int n_real, const uint64_t* seed_dev,
-                              int64_t total, float* xr, cudaStream_t st) {
+                              int64_t total, float* xr, float4* recB, cudaStream_t st) {
     dim3 grid((unsigned)n_curves, (unsigned)n_real);
-    noise_prep_kernel<<<grid, kNoiseThreads, 0, st>>>(off, seed_dev, total, xr);
+    noise_prep_kernel<<<grid, kNoiseThreads, 0, st>>>(off, seed_dev, total, xr, n_real == 1 ? recB : nullptr);
     return cudaGetLastError();
 }
 

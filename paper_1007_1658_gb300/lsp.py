@@ -39,7 +39,8 @@ class LspError(RuntimeError):
 class lsp_options(ctypes.Structure):
     _fields_ = [("sincos_mode", ctypes.c_int32), ("phase_mode", ctypes.c_int32),
                 ("freqs_per_thread", ctypes.c_int32), ("split", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("mlp_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("timing", ctypes.c_int32), ("mlp_fp32", ctypes.c_int32), ("batch_rhs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 def load():

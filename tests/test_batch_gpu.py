@@ -165,3 +165,26 @@ def test_noise_periodograms_follow_the_beta_law(ctx):
               P_out=P, P_off=P_off)
     z = 2 * P.astype(np.float64) / N
     assert stats.kstest(z, stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("R,F", [(2, 8), (4, 8), (8, 4)])
+def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F):
+    """Groups of R realizations share the phase, the recurrence and CC/CS; each
+    (frequency, realization) must come out bit for bit as the one-at-a-time
+    kernel with the same strip length computes it (here with a partial last
+    group)."""
+    b = _small_batch(n_curves=9, seed=31)
+    n_real = R + R // 2 + 1
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    outs = []
+    for rhs in (1, R):
+        ctx = lsp.Context(0, sincos_mode=3, freqs_per_thread=F, batch_rhs=rhs)
+        P = np.empty(n_real * int(P_off[-1]), np.float32)
+        mx = np.empty(n_real * b.n, np.float32)
+        am = np.empty(n_real * b.n, np.int32)
+        ctx.batch(b.t_off, b.t, b.f0, b.df, b.nf, seed=77, n_real=n_real, P_out=P, P_off=P_off, maxP=mx, argmax=am)
+        outs.append((P, mx, am))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
