@@ -57,7 +57,7 @@ def _peaks():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("ls_main.cu", "lsp_kernels.cuh"):
+    for f in ("ls_main.cu", "ls_device.cuh", "lsp_kernels.cuh"):
         with open(os.path.join(ROOT, "paper_1007_1658_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -15,6 +15,8 @@ arrays.  Every routine cites the passage of the paper it follows:
 * ``grid``                 -- Eq. 9-11
 * ``periodogram_fp32phase_at`` -- the paper's single-precision phase (Sec. 4.3)
 * ``window_at``            -- spectral window (|sum exp(2 pi i f t)|^2 / N^2)
+* ``gls_at`` / ``gls_lsq`` -- floating-mean weighted periodogram (Sec. 6.3) and its
+  brute-force least-squares reading
 * ``philox4x32_10`` / ``noise`` -- counter-based Gaussian noise for Sec. 6.2's
   Monte-Carlo use (Salmon et al. 2011; Box & Muller 1958)
 
@@ -78,11 +80,13 @@ def _load():
         lib.oracle_window_at.argtypes = [p, i64, p, i64, p]
         lib.oracle_philox4x32_10.argtypes = [p, p, p]
         lib.oracle_philox4x32_10.restype = None
+        lib.oracle_gls_at.argtypes = [p, p, p, i64, p, i64, p]
+        lib.oracle_gls_lsq.argtypes = [p, p, p, i64, d, p]
         lib.oracle_noise.argtypes = [u64, u32, u32, i64, p]
         lib.oracle_noise.restype = None
         for name in ("oracle_normalize", "oracle_periodogram_at", "oracle_periodogram",
                      "oracle_periodogram_refac_at", "oracle_lsq_power", "oracle_grid",
-                     "oracle_periodogram_fp32phase_at", "oracle_window_at"):
+                     "oracle_periodogram_fp32phase_at", "oracle_window_at", "oracle_gls_at", "oracle_gls_lsq"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -182,6 +186,26 @@ def window_at(t, freqs):
     W = np.empty(freqs.size, dtype=np.float64)
     _check(_load().oracle_window_at(_ptr(t), t.size, _ptr(freqs), freqs.size, _ptr(W)))
     return W
+
+
+def gls_at(t, X, freqs, dy=None):
+    """Floating-mean (generalized) periodogram, (N/2) p, at arbitrary frequencies (Sec. 6.3)."""
+    t, X, freqs = _f64(t), _f64(X), _f64(freqs)
+    dyp = None if dy is None else _f64(dy)
+    P = np.empty(freqs.size, dtype=np.float64)
+    _check(_load().oracle_gls_at(_ptr(t), _ptr(X), None if dyp is None else _ptr(dyp), t.size, _ptr(freqs),
+                                 freqs.size, _ptr(P)))
+    return P
+
+
+def gls_lsq(t, X, f, dy=None):
+    """Brute-force 3-parameter weighted least-squares reading of gls_at (tiny inputs)."""
+    t, X = _f64(t), _f64(X)
+    dyp = None if dy is None else _f64(dy)
+    P = ctypes.c_double()
+    _check(_load().oracle_gls_lsq(_ptr(t), _ptr(X), None if dyp is None else _ptr(dyp), t.size, float(f),
+                                  ctypes.byref(P)))
+    return P.value
 
 
 def philox4x32_10(ctr, key):

@@ -427,3 +427,156 @@ void oracle_noise(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, doubl
         for (int i = 0; i < 4 && b * 4 + i < n; ++i) x[b * 4 + i] = z[i];
     }
 }
+
+/*
+ * Floating-mean ("generalized") periodogram, the extension Sec. 6.3 points at
+ * (Zechmeister & Kuerster 2009; Shrager 2001): the sinusoid is fitted together
+ * with an offset, with weights w_j = (1/dy_j^2) / sum(1/dy^2) (w_j = 1/N_t
+ * without errors).  With Y = sum w y, C = sum w cos wt, S = sum w sin wt and
+ * YC = sum w y cos - Y C, YS = sum w y sin - Y S, CC = sum w cos^2 - C^2,
+ * SS = sum w sin^2 - S^2, CS = sum w cos sin - C S, YY = sum w y^2 - Y^2 and
+ * D = CC SS - CS^2, the fraction of the weighted variance that the fit removes
+ * is p = (SS YC^2 + CC YS^2 - 2 CS YC YS) / (YY D), in [0, 1].  It is reported
+ * as P = (N_t / 2) p, the scale of Eq. 1's P_n: at frequencies where C = S = 0
+ * with equal weights the two periodograms coincide.
+ *
+ * Rank-deficient frequencies (reading): when cos and sin, once centred, are
+ * linearly dependent on the samples (D <= 2^-40, e.g. the Nyquist frequency
+ * of an even grid, where every sin vanishes), the fit is the projection on the
+ * one remaining direction, p = (YC^2 + YS^2) / (YY (CC + SS)); when both vanish
+ * (CC + SS <= 2^-40, e.g. f = 0) p = 0.  This is what the least-squares fit
+ * itself gives (the data vector (YC, YS) always lies in the range of the 2x2
+ * matrix [[CC, CS], [CS, SS]]), and it parallels the classic periodogram's
+ * treatment of a vanishing denominator.
+ */
+static int gls_weights(const double *dy, int64_t n, double *w)
+{
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (dy) {
+            if (!isfinite(dy[j]) || !(dy[j] > 0.0)) return OR_BAD_ARG;
+            w[j] = 1.0 / (dy[j] * dy[j]);
+        } else {
+            w[j] = 1.0;
+        }
+        s += w[j];
+    }
+    for (int64_t j = 0; j < n; ++j) w[j] /= s;
+    return OR_OK;
+}
+
+int oracle_gls_at(const double *t, const double *X, const double *dy, int64_t n,
+                  const double *freqs, int64_t nf, double *P)
+{
+    if (n < 3 || nf < 0 || !t || !X || (nf > 0 && (!freqs || !P))) return OR_BAD_ARG;
+    for (int64_t j = 0; j < n; ++j)
+        if (!isfinite(t[j]) || !isfinite(X[j])) return OR_NONFINITE;
+    for (int64_t k = 0; k < nf; ++k)
+        if (!isfinite(freqs[k])) return OR_NONFINITE;
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    double *tt = (double *)malloc((size_t)n * sizeof(double));
+    if (!w || !tt) { free(w); free(tt); return OR_NOMEM; }
+    int st = gls_weights(dy, n, w);
+    if (st != OR_OK) { free(w); free(tt); return st; }
+    double t0 = min_time(t, n);
+    for (int64_t j = 0; j < n; ++j) tt[j] = t[j] - t0;
+    nsum ys = {0, 0}, yys = {0, 0};
+    for (int64_t j = 0; j < n; ++j) { nsum_add(&ys, w[j] * X[j]); nsum_add(&yys, w[j] * X[j] * X[j]); }
+    const double Y = nsum_value(&ys);
+    /* YY in two passes: sum w (y - Y)^2 */
+    nsum yv = {0, 0};
+    for (int64_t j = 0; j < n; ++j) { double d = X[j] - Y; nsum_add(&yv, w[j] * d * d); }
+    const double YY = nsum_value(&yv);
+    if (!(YY > 0.0)) { free(w); free(tt); return OR_DEGENERATE; }
+    const double thr = ldexp(1.0, -40);
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < nf; ++k) {
+        nsum c = {0, 0}, s = {0, 0}, yc = {0, 0}, ysn = {0, 0}, cc = {0, 0}, ss = {0, 0}, cs = {0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double arg = TWO_PI * reduced_turns(freqs[k], tt[j]);
+            double co = cos(arg), si = sin(arg);
+            nsum_add(&c, w[j] * co);
+            nsum_add(&s, w[j] * si);
+            nsum_add(&yc, w[j] * X[j] * co);
+            nsum_add(&ysn, w[j] * X[j] * si);
+            nsum_add(&cc, w[j] * co * co);
+            nsum_add(&ss, w[j] * si * si);
+            nsum_add(&cs, w[j] * co * si);
+        }
+        double C = nsum_value(&c), S = nsum_value(&s);
+        double YC = nsum_value(&yc) - Y * C, YS = nsum_value(&ysn) - Y * S;
+        double CC = nsum_value(&cc) - C * C, SS = nsum_value(&ss) - S * S, CS = nsum_value(&cs) - C * S;
+        double D = CC * SS - CS * CS;
+        double p = 0.0;
+        if (D > thr)
+            p = (SS * YC * YC + CC * YS * YS - 2.0 * CS * YC * YS) / (YY * D);
+        else if (CC + SS > thr)
+            p = (YC * YC + YS * YS) / (YY * (CC + SS));
+        P[k] = 0.5 * (double)n * p;
+    }
+    free(w);
+    free(tt);
+    return OR_OK;
+}
+
+/*
+ * Brute-force reading of the floating-mean periodogram, independent of the
+ * closed form above: the weighted least-squares fit of the data by the span of
+ * {1, cos wt, sin wt}, found by modified Gram-Schmidt (two sweeps) in the
+ * weighted inner product, in long double; a basis vector whose remainder has
+ * weighted length below 2^-30 adds nothing (rank-deficient frequencies).
+ * P = (N_t/2) (1 - chi2_fit / chi2_offset).  Tiny n only.
+ */
+int oracle_gls_lsq(const double *t, const double *X, const double *dy, int64_t n, double f, double *P)
+{
+    if (n < 3 || !t || !X || !P) return OR_BAD_ARG;
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    long double *Q = (long double *)malloc((size_t)(4 * n) * sizeof(long double));
+    if (!w || !Q) { free(w); free(Q); return OR_NOMEM; }
+    int st = gls_weights(dy, n, w);
+    if (st != OR_OK) { free(w); free(Q); return st; }
+    const long double tp = 6.283185307179586476925286766559L;
+    long double t0 = (long double)min_time(t, n);
+    long double *r = Q + 3 * n; /* residual of the data */
+    for (int64_t j = 0; j < n; ++j) {
+        long double ph = (long double)f * ((long double)t[j] - t0);
+        ph -= nearbyintl(ph);
+        Q[j] = 1.0L;
+        Q[n + j] = cosl(tp * ph);
+        Q[2 * n + j] = sinl(tp * ph);
+        r[j] = X[j];
+    }
+    int kept[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        long double *qa = Q + a * n;
+        for (int sweep = 0; sweep < 2; ++sweep)
+            for (int b = 0; b < a; ++b) {
+                if (!kept[b]) continue;
+                long double *qb = Q + b * n, d = 0;
+                for (int64_t j = 0; j < n; ++j) d += w[j] * qa[j] * qb[j];
+                for (int64_t j = 0; j < n; ++j) qa[j] -= d * qb[j];
+            }
+        long double len = 0;
+        for (int64_t j = 0; j < n; ++j) len += w[j] * qa[j] * qa[j];
+        /* dependent on the earlier ones (or nothing but rounding: the basis
+         * vectors have weighted length <= 1, so the test is absolute) */
+        if (!(len > 0x1p-60L)) continue;
+        long double inv = 1.0L / sqrtl(len);
+        for (int64_t j = 0; j < n; ++j) qa[j] *= inv;
+        kept[a] = 1;
+    }
+    /* chi2 of the offset-only fit (first basis vector) and of the full fit */
+    long double chi0 = 0, chi = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!kept[a]) continue;
+        long double *qa = Q + a * n, d = 0;
+        for (int64_t j = 0; j < n; ++j) d += w[j] * r[j] * qa[j];
+        for (int64_t j = 0; j < n; ++j) r[j] -= d * qa[j];
+        if (a == 0) for (int64_t j = 0; j < n; ++j) chi0 += w[j] * r[j] * r[j];
+    }
+    for (int64_t j = 0; j < n; ++j) chi += w[j] * r[j] * r[j];
+    *P = (double)(0.5L * (long double)n * (1.0L - chi / chi0));
+    free(w);
+    free(Q);
+    return OR_OK;
+}
