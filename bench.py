@@ -235,22 +235,26 @@ def run_gpu(args, rank, world, dist):
     peaks, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mode = args.mode if args.mode else lsp.SINCOS_RECUR3
-    F = args.F if args.F else {lsp.SINCOS_MUFU: 8, lsp.SINCOS_RECUR: 16, lsp.SINCOS_RECUR3: 24}[mode]
+    F = args.F if args.F else {lsp.SINCOS_MUFU: 8, lsp.SINCOS_RECUR: 16, lsp.SINCOS_RECUR3: 24,
+                               lsp.SINCOS_RECUR3_X2: 24}[mode]
     # algorithmic work per term on the bounding pipe (roof in terms per clock per SM)
     roof = {lsp.SINCOS_MUFU: (2, "SFU (MUFU): 2 sin/cos ops per term, 16 ops/clk/SM", 16.0 / 2),
             lsp.SINCOS_RECUR: (8, "FMA pipe: 4 accumulate + 4 rotation FP32 ops per term, 128/clk/SM", 128.0 / 8),
             lsp.SINCOS_RECUR3: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 ops per term, 128/clk/SM",
-                                128.0 / 6)}[mode]
+                                128.0 / 6),
+            lsp.SINCOS_RECUR3_X2: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 lane ops per term (as FFMA2 "
+                                      "pairs + 2 FFMA), 128/clk/SM", 128.0 / 6)}[mode]
     terms_per_clk = roof[2]
     peak = terms_per_clk * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
-    kernel = "ls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4}[mode])
+    kernel = "ls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N_t": int(c.t.size), "N_f": int(c.nf), "terms_per_step": terms,
-                   "sincos": {1: "mufu", 2: "recurrence", 3: "three-term recurrence"}[mode], "F": F,
+                   "sincos": {1: "mufu", 2: "recurrence", 3: "three-term recurrence",
+                              4: "three-term recurrence, packed FP32x2"}[mode], "F": F,
                    "phase": "fixed64",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "frequency shards x%d" % world},
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e9, "peak": peak / 1e9,
@@ -268,6 +272,10 @@ def run_gpu(args, rank, world, dist):
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(c, args.cpu_bins).items() if k != "seconds"}
     if args.batch:
         line["batched_mc"] = run_batch_bench(ctx, torch, dev, stream, args)
+    if args.gls:
+        line["floating_mean"] = run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms)
+    if args.paper:
+        line["paper_shape"] = run_paper_shape(torch, dev, stream, args, peaks, sms)
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -289,6 +297,119 @@ def _e2e(lsp, torch, c, f0, local, stream, args, world):
         e2e_s.append(time.perf_counter() - t0)
     ctx_h.close()
     return world * terms * len(e2e_s) / sum(e2e_s)
+
+
+def _time_calls(torch, stream, fn, warmup, steps, flush):
+    """Median device time (ms) of fn() over `steps` calls after `warmup`, L2
+    flushed before each, CUDA events on the launching stream."""
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def run_paper_shape(torch, dev, stream, args, peaks, sms):
+    """The paper's benchmark shape (Sec. 5.2-5.3) on synthetic data: N_t =
+    382,003 samples over 150 d, N_f = 1,528,064 (5.84e11 terms), one call, and
+    the N_t sweep of its Fig. 4 (uniform down-sampling by 2^k, N_f = 4 N_t
+    rounded up to 256), with the oracle timed on the host cores at the small
+    end.  The paper's Tesla C1060 took 20.3 s for its 382,003-sample curve
+    (another machine and FP32 phases: context, not a target)."""
+    from paper_1007_1658_gb300 import lsp, synth
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx = lsp.Context(dev.index or 0, stream=stream)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sweep = []
+    with ClockSampler(dev.index or 0) as clk:
+        for step in (256, 128, 64, 32, 16, 8, 4, 2, 1):
+            c = synth.corot_382k(step=step)
+            t_d, X_d = d(c.t), d(c.X)
+            P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
+            fn = lambda: ctx.periodogram(t_d, X_d, c.f0, c.df, c.nf, out=P_d)
+            ms = _time_calls(torch, stream, fn, 2, 3, flush)
+            row = {"N_t": int(c.t.size), "N_f": int(c.nf), "terms": c.terms, "gpu_ms": ms,
+                   "gpu_terms_per_s": c.terms / (ms * 1e-3)}
+            if args.cpu_baseline and c.terms <= 2e8:
+                import oracle
+                t0 = time.perf_counter()
+                oracle.periodogram(c.t, c.X, c.f0, c.df, c.nf)
+                row["cpu_oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+            sweep.append(row)
+        ctx.sync(120.0)
+    ctx.close()
+    full = sweep[-1]
+    big = sweep[-4:]
+    slope = float(np.polyfit(np.log([r["N_t"] for r in big]), np.log([r["gpu_ms"] for r in big]), 1)[0])
+    import oracle
+    return {"workload": "corot_382k: N_t = 382,003 over 150 d (32-s slots, orbit gaps), N_f = 1,528,064, "
+                        "f_0 = df = 1/(4T); sweep by uniform down-sampling",
+            "t_calc_s": full["gpu_ms"] * 1e-3, "terms_per_s": full["gpu_terms_per_s"],
+            "paper_c1060_t_calc_s": 20.3, "paper_8core_cpu_t_calc_s": 566.0,
+            "slope_dlog_t_dlog_Nt_top4": slope, "sweep": sweep,
+            "cpu_cores": oracle.num_threads() if args.cpu_baseline else None, "clocks": clk.summary()}
+
+
+def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
+    """Floating-mean (generalized, weighted) periodogram on gapped_100k with
+    per-sample errors (same times and grid): device-resident inputs, L2
+    flushed between steps, CUDA events on the launching stream."""
+    from paper_1007_1658_gb300 import lsp, synth
+    c = synth.with_errors(synth.gapped_100k)
+    if args.nf:
+        c.nf = int(args.nf)
+    terms = c.t.size * c.nf
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    t_d, X_d, dy_d = d(c.t), d(c.X), d(c.dy)
+    P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    mode = args.mode if args.mode else lsp.SINCOS_RECUR3_X2
+    gctx = lsp.Context(dev.index or 0, stream=stream, timing=1, sincos_mode=mode,
+                       freqs_per_thread=args.F if args.F in (8, 16) else 0)
+    F = args.F if args.F in (8, 16) else (8 if mode == lsp.SINCOS_MUFU else 16)
+    steps = max(3, args.steps)
+    with torch.cuda.stream(stream), ClockSampler(dev.index or 0) as clk:
+        for _ in range(args.warmup):
+            gctx.periodogram_gls(t_d, X_d, c.f0, c.df, c.nf, dy=dy_d, out=P_d)
+        gctx.sync(120.0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        main_ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            gctx.periodogram_gls(t_d, X_d, c.f0, c.df, c.nf, dy=dy_d, out=P_d)
+            ev[i][1].record(stream)
+            main_ms.append(gctx.last_timing()[1])
+        gctx.sync(120.0)
+    torch.cuda.synchronize(dev)
+    gctx.close()
+    step_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # bounding pipe per term: 6 accumulating FMA + the sin/cos of the mode
+    roof = {lsp.SINCOS_MUFU: ("SFU (MUFU): 2 sin/cos ops per term, 16 ops/clk/SM", 16.0 / 2),
+            lsp.SINCOS_RECUR: ("FMA pipe: 6 accumulate + 4 rotation FP32 ops per term, 128/clk/SM", 128.0 / 10),
+            lsp.SINCOS_RECUR3: ("FMA pipe: 6 accumulate + 2 three-term FP32 ops per term, 128/clk/SM",
+                                128.0 / 8),
+            lsp.SINCOS_RECUR3_X2: ("FMA pipe: 6 accumulate + 2 three-term FP32 lane ops per term (FFMA2 pairs "
+                                   "+ 2 FFMA), 128/clk/SM", 128.0 / 8)}[mode]
+    peak = roof[1] * sms * peaks["sm_max_mhz"] * 1e6
+    achieved = terms / (float(np.mean(main_ms)) * 1e-3)
+    return {"workload": "gapped_100k with per-sample errors (dy log-U[0.15, 1.5], 2%% x10), N_t = %d, N_f = %d"
+                        % (c.t.size, c.nf),
+            "ms_per_call": step_ms, "terms_per_s": terms / (step_ms * 1e-3),
+            "roofline": {"bound": "alu", "kernel": "gls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode]),
+                         "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterms/s", "frac": achieved / peak,
+                         "peak_basis": "%s: %.2f terms/clk/SM x %d SMs x %.0f MHz (%s sm_max_mhz)" % (
+                             roof[0], roof[1], sms, peaks["sm_max_mhz"], peak_src),
+                         "main_ms": float(np.mean(main_ms))},
+            "clocks": clk.summary()}
 
 
 def run_batch_bench(ctx, torch, dev, stream, args):
@@ -375,6 +496,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-gls", dest="gls", action="store_false", help="skip the floating-mean periodogram leg")
+    ap.add_argument("--no-paper", dest="paper", action="store_false", help="skip the paper-shape N_t sweep")
     ap.add_argument("--nf", type=int, default=0, help="override N_f (smaller profiling case)")
     ap.add_argument("--batch-curves", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=3)

@@ -54,9 +54,13 @@ typedef enum lsp_sincos_mode {
     LSP_SINCOS_MUFU = 1,   /* hardware sin/cos (SFU) of every phase (Sec. 4.3's choice)  */
     LSP_SINCOS_RECUR = 2,  /* SFU seed per strip of adjacent frequencies, then the
                               angle-addition rotation by (cos, sin)(2 pi t_j df) on FMA */
-    LSP_SINCOS_RECUR3 = 3  /* SFU seed, one rotation, then the three-term form
+    LSP_SINCOS_RECUR3 = 3, /* SFU seed, one rotation, then the three-term form
                               z_{k+1} = 2 cos(2 pi t_j df) z_k - z_{k-1} (half the FMA work
                               of RECUR; error grows faster with the strip length)      */
+    LSP_SINCOS_RECUR3_X2 = 4 /* RECUR3 with the (cos, sin) pair in packed FP32x2 FMA:
+                              the same roundings (bit-identical results), fewer
+                              instructions per term; the multi-realization batch
+                              kernels use the scalar form                              */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */
@@ -114,6 +118,29 @@ lsp_status lsp_set_stream(lsp_ctx *ctx, void *cuda_stream);
  */
 lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64_t N_t,
                            double f_0, double df, int64_t N_f, float *P_out);
+
+/*
+ * Floating-mean ("generalized") periodogram on the same grid: the extension
+ * Sec. 6.3 names (Shrager 2001; Zechmeister & Kuerster 2009), where the mean is
+ * fitted together with the sinusoid rather than removed beforehand, and each
+ * sample carries the weight w_j = (1/dy_j^2) / sum(1/dy^2) (equal weights when
+ * dy is NULL).  With p(f) the fraction of the weighted variance of X that the
+ * best fit a cos 2 pi f t + b sin 2 pi f t + c removes (0 <= p <= 1):
+ *     P_out[k] = (N_t / 2) p(f_0 + k df),
+ * the scale of lsp_periodogram's P_n (the two agree where sum w cos and
+ * sum w sin vanish, e.g. Fourier frequencies of an even grid).  Where the
+ * centred cos and sin are linearly dependent on the samples (f = 0, Nyquist
+ * of an even grid) the fit uses the remaining direction; where both vanish,
+ * P = 0.  Same t, X, grid and pointer rules as lsp_periodogram; dy[N_t]
+ * (FP64, optional, host or device) must be finite and > 0.  N_t >= 3.
+ * sincos_mode selects MUFU, RECUR, RECUR3 or RECUR3_X2 (AUTO: RECUR3_X2);
+ * strips are 8 or 16 frequencies (freqs_per_thread 8 or 16; other values use
+ * 16, 8 for MUFU).
+ * Errors: INVALID_ARG (also a bad dy, on the device), NONFINITE, DEGENERATE,
+ * UNSUPPORTED (phase_mode NAIVE_FP32), OOM, CUDA.
+ */
+lsp_status lsp_periodogram_gls(lsp_ctx *ctx, const double *t, const double *X, const double *dy,
+                               int64_t N_t, double f_0, double df, int64_t N_f, float *P_out);
 
 /*
  * Many periodograms in one call: measured curves, or Monte-Carlo noise

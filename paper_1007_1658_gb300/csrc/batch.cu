@@ -182,6 +182,7 @@ BatchFn batch_fn_x(int mode, int F) {
         case kMufu: return batch_fn_f<kMufu, XREC>(F);
         case kRecur: return batch_fn_f<kRecur, XREC>(F);
         case kRecur3: return batch_fn_f<kRecur3, XREC>(F);
+        case kRecur3x2: return batch_fn_f<kRecur3x2, XREC>(F);
         default: return nullptr;
     }
 }
@@ -203,7 +204,8 @@ MrhsFn mrhs_fn(int mode, int F, int R) {
     switch (mode) {
         case kMufu: return mrhs_fn_f<kMufu>(F, R);
         case kRecur: return mrhs_fn_f<kRecur>(F, R);
-        case kRecur3: return mrhs_fn_f<kRecur3>(F, R);
+        case kRecur3:
+        case kRecur3x2: return mrhs_fn_f<kRecur3>(F, R);  // shared-recurrence strips use the scalar form
         default: return nullptr;
     }
 }

@@ -1,0 +1,281 @@
+// gls.cu -- the floating-mean (generalized, weighted) periodogram: the
+// extension of the sums of Eq. 8 that Sec. 6.3 points to (Shrager 2001;
+// Zechmeister & Kuerster 2009), where a constant offset is fitted together
+// with the sinusoid and each sample carries the weight w_j = (1/dy_j^2) /
+// sum(1/dy^2).
+//
+// With centred, weighted data the sums needed per frequency are
+//   YC = sum w y' cos,  YS = sum w y' sin         (y' = y - sum w y)
+//   C  = sum w cos,     S  = sum w sin
+//   CC' = sum w cos^2,  CS' = sum w cos sin       (SS' = 1 - CC')
+// and the centred second moments CC = CC' - C^2, SS = SS' - S^2,
+// CS = CS' - C S.  The power is the fraction p of the weighted variance
+// removed by the best fit a cos + b sin + c, reported as P = (N_t / 2) p.
+//
+// Per-sample records are the classic ones (fixed-point phases, rotation) with
+// x = q (y - mean_w) / sd_w and a second stream q_j = sqrt(w_j).  The sin/cos
+// seed of each strip is scaled by q once per sample; the recurrences are
+// linear, so every later term of the strip carries the factor q too, and
+// with c~ = q cos, s~ = q sin the six running sums are
+//   XC += x c~, XS += x s~, C += q c~, S += q s~, CC' += c~ c~, CS' += c~ s~
+// -- six FMA per term plus the recurrence (2 FMA in the three-term form):
+// 8 FMA-pipe ops per term against 6 for the classic periodogram.
+//
+// Closed form of p (same algebra as Eq. 5-6 with the trace CC + SS in place
+// of N_t): the 2x2 matrix [[CC, CS], [CS, SS]] has eigenvalues (T +- R)/2,
+// T = CC + SS, R = |CC - SS + 2i CS|; rotating (YC, YS) onto its eigenvectors
+// gives p = num1/den1 + num2/den2 (data variance normalized to 1).  A
+// direction whose eigenvalue is at the FP32 rounding level (f = 0, the
+// Nyquist frequency of an even grid, two-phase sampling) adds nothing: the
+// fit is the projection on the remaining direction.
+#include "ls_device.cuh"
+
+namespace lsp {
+namespace {
+
+using namespace dev;
+
+constexpr int kGlsSums = kGlsRows;
+
+template <int F, int MODE>
+struct GStrip {
+    float xc[F], xs[F], c1[F], s1[F], cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) xc[i] = xs[i] = c1[i] = s1[i] = cc[i] = cs[i] = 0.f;
+    }
+
+    __device__ __forceinline__ void acc(int i, float x, float q, float c, float s) {
+        xc[i] = fmaf(x, c, xc[i]);
+        xs[i] = fmaf(x, s, xs[i]);
+        c1[i] = fmaf(q, c, c1[i]);
+        s1[i] = fmaf(q, s, s1[i]);
+        cc[i] = fmaf(c, c, cc[i]);
+        cs[i] = fmaf(c, s, cs[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
+        uint32_t p = top_phase(A, k0);
+        if (MODE == kMufu) {
+            const uint32_t du = __float_as_uint(B.w);
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float s, c;
+                __sincosf(phase_to_angle(p), &s, &c);
+                acc(i, x, q, q * c, q * s);
+                p += du;
+            }
+        } else {
+            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            float s, c;
+            __sincosf(phase_to_angle(p), &s, &c);
+            c *= q;
+            s *= q;
+            float cp = c, sp = s;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                acc(i, x, q, c, s);
+                if (i + 1 < F) {
+                    float cn, sn;
+                    if (MODE == kRecur || i == 0) {
+                        cn = fmaf(c, C, -s * S);
+                        sn = fmaf(s, C, c * S);
+                    } else {
+                        cn = fmaf(C2, c, -cp);
+                        sn = fmaf(C2, s, -sp);
+                    }
+                    cp = c;
+                    sp = s;
+                    c = cn;
+                    s = sn;
+                }
+            }
+        }
+    }
+};
+
+// Packed form of the three-term strip (see Strip<F, kRecur3x2>): the pairs
+// (XC, XS) and (C, S) take one FFMA2 each per term with the data factors +-x
+// and +-q, CC' and CS' two scalar FFMA, the recurrence one FFMA2.
+template <int F>
+struct GStrip<F, kRecur3x2> {
+    float xc[F], xs[F], c1[F], s1[F], cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) xc[i] = xs[i] = c1[i] = s1[i] = cc[i] = cs[i] = 0.f;
+    }
+
+    __device__ __forceinline__ void acc(int i, float2 xf, float2 qf, float2 y) {
+        const float2 a = __ffma2_rn(xf, y, make_float2(xc[i], xs[i]));
+        xc[i] = a.x;
+        xs[i] = a.y;
+        const float2 b = __ffma2_rn(qf, y, make_float2(c1[i], s1[i]));
+        c1[i] = b.x;
+        s1[i] = b.y;
+        cc[i] = fmaf(y.x, y.x, cc[i]);
+        cs[i] = fmaf(y.x, y.y, cs[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
+        const uint32_t p = top_phase(A, k0);
+        const float C = B.y, S = B.z, C2 = 2.f * B.y;
+        float s, c;
+        __sincosf(phase_to_angle(p), &s, &c);
+        c *= q;
+        s *= q;
+        const float2 xp = make_float2(x, x), xn = make_float2(-x, -x);
+        const float2 qp = make_float2(q, q), qn = make_float2(-q, -q);
+        const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
+        float2 y0 = make_float2(c, s);
+        acc(0, xp, qp, y0);
+        if (F == 1) return;
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, xp, qp, y1);
+#pragma unroll
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            const bool neg = (i >> 1) & 1;
+            acc(i, neg ? xn : xp, neg ? qn : qp, y2);
+            y0 = y1;
+            y1 = y2;
+        }
+    }
+};
+
+// p from the six sums (weights summing to 1, data variance 1), in FP64.
+__device__ __forceinline__ float gls_value(double XC, double XS, double C, double S, double CCp, double CSp,
+                                           double n) {
+    const double CC = CCp - C * C;
+    const double SS = (1.0 - CCp) - S * S;
+    const double CS = CSp - C * S;
+    const double A = CC - SS, B = 2.0 * CS;
+    const double T = CC + SS;
+    const double R = sqrt(A * A + B * B);
+    double c2 = 1.0, s2 = 0.0;
+    if (R > 0.0) {
+        c2 = A / R;
+        s2 = B / R;
+    }
+    const double z2 = XC * XC + XS * XS;
+    const double cross = c2 * (XC * XC - XS * XS) + s2 * (2.0 * XC * XS);
+    const double num1 = fmax(0.5 * (z2 + cross), 0.0);
+    const double num2 = fmax(0.5 * (z2 - cross), 0.0);
+    const double den1 = 0.5 * (T + R);
+    const double den2 = 0.5 * (T - R);
+    const double thr = 0x1p-24;
+    double p = 0.0;
+    if (den1 > thr) p += num1 / den1;
+    if (den2 > thr) p += num2 / den2;
+    return (float)(0.5 * n * p);
+}
+
+template <int F, int MODE>
+__global__ void __launch_bounds__(kMainThreads)
+gls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ q,
+                int64_t N, int64_t chunk, int N_f, int64_t nf_pad, float* __restrict__ part,
+                float* __restrict__ P_out) {
+    __shared__ __align__(16) TileSmemN<1> sm;
+    const uint32_t k0 = (uint32_t)blockIdx.x * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+    const int64_t j0 = (int64_t)blockIdx.y * chunk;
+    const int64_t j1 = min(N, j0 + chunk);
+    GStrip<F, MODE> st;
+    st.zero();
+    for_each_tile_n<1>(sm, recA, recB, q, 0, 1, j0, j1,
+                       [&](const uint4* a, const float4* b, const float (*qs)[kTile], int n) {
+#pragma unroll 2
+                           for (int j = 0; j < n; ++j) {
+                               const float4 B = b[j];
+                               st.add(a[j], B, B.x, qs[0][j], k0);
+                           }
+                       });
+    if (P_out) {
+#pragma unroll
+        for (int i = 0; i < F; ++i)
+            if (k0 + i < (uint32_t)N_f)
+                P_out[k0 + i] = gls_value(st.xc[i], st.xs[i], st.c1[i], st.s1[i], st.cc[i], st.cs[i], (double)N);
+        return;
+    }
+    float* base = part + (size_t)blockIdx.y * kGlsSums * (size_t)nf_pad + k0;
+    auto row = [&](int r, const float (&v)[F]) {
+#pragma unroll
+        for (int i = 0; i < F; i += 4)
+            *reinterpret_cast<float4*>(base + (size_t)r * nf_pad + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    };
+    row(0, st.xc);
+    row(1, st.xs);
+    row(2, st.c1);
+    row(3, st.s1);
+    row(4, st.cc);
+    row(5, st.cs);
+}
+
+// Per-chunk partial sums added in chunk order in FP64 (deterministic), then p.
+__global__ void __launch_bounds__(256)
+gls_finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, int N_f, double n,
+                    float* __restrict__ P_out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N_f) return;
+    double s[kGlsSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int sp = 0; sp < split; ++sp) {
+        const float* p = part + (size_t)sp * kGlsSums * (size_t)nf_pad + k;
+#pragma unroll
+        for (int r = 0; r < kGlsSums; ++r) s[r] += (double)p[(size_t)r * nf_pad];
+    }
+    P_out[k] = gls_value(s[0], s[1], s[2], s[3], s[4], s[5], n);
+}
+
+using GlsFn = void (*)(const uint4*, const float4*, const float*, int64_t, int64_t, int, int64_t, float*, float*);
+
+template <int MODE>
+GlsFn gls_fn_f(int F) {
+    switch (F) {
+        case 8: return gls_main_kernel<8, MODE>;
+        case 16: return gls_main_kernel<16, MODE>;
+        default: return nullptr;
+    }
+}
+
+GlsFn gls_fn(int mode, int F) {
+    switch (mode) {
+        case kMufu: return gls_fn_f<kMufu>(F);
+        case kRecur: return gls_fn_f<kRecur>(F);
+        case kRecur3: return gls_fn_f<kRecur3>(F);
+        case kRecur3x2: return gls_fn_f<kRecur3x2>(F);
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+int gls_occupancy(int mode, int F) {
+    const GlsFn fn = gls_fn(mode, F);
+    if (!fn) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kMainThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB, const float* q, int64_t N,
+                       int64_t N_f, float* part, float* P_out, cudaStream_t st) {
+    const GlsFn fn = gls_fn(s.mode, s.F);
+    if (!fn) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)s.nfb, (unsigned)s.split);
+    fn<<<grid, kMainThreads, 0, st>>>(recA, recB, q, N, s.chunk, (int)N_f, s.nf_pad, part,
+                                      s.split == 1 ? P_out : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gls_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f, float* P_out,
+                                cudaStream_t st) {
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((N_f + threads - 1) / threads);
+    gls_finalize_kernel<<<blocks, threads, 0, st>>>(part, s.split, s.nf_pad, (int)N_f, (double)N, P_out);
+    return cudaGetLastError();
+}
+
+}  // namespace lsp

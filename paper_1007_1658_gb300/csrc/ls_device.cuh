@@ -15,7 +15,13 @@ constexpr float kTwoPi = 6.28318530717958647692f;
 constexpr float kThreePi = 9.42477796076937971538f;
 
 // Internal kernel modes (the kMode* values of lsp_kernels.cuh).
-enum : int { kMufu = kModeMufu, kRecur = kModeRecur, kNaive = kModeNaive, kRecur3 = kModeRecur3 };
+enum : int {
+    kMufu = kModeMufu,
+    kRecur = kModeRecur,
+    kNaive = kModeNaive,
+    kRecur3 = kModeRecur3,
+    kRecur3x2 = kModeRecur3x2
+};
 
 // Top 23 bits of a 32-bit turn fraction, offset by half a turn at prep time,
 // become a float in [1, 2) by pasting them under the exponent of 1.0; one FMA
@@ -24,11 +30,15 @@ __device__ __forceinline__ float phase_to_angle(uint32_t p) {
     return fmaf(__uint_as_float(0x3F800000u | (p >> 9)), kTwoPi, -kThreePi);
 }
 
-// Top 32 bits of the phase v + k u (mod 2^64) of record A at frequency k.
+// Top 32 bits of the phase v + k u (mod 2^64) of record A at frequency k,
+// from 32-bit products: v_hi + k u_hi + hi(k u_lo).  The carry of the low
+// word (v_lo + lo(k u_lo)) is left out, so the result is the exact top word
+// or one less: an error below 2^-32 turn, far under the 2^-23-turn step of
+// the FP32 angle taken from it (the 2^40 rounding offset in v sits in the top
+// word and still rounds that step).  A short dependency chain (two IMAD)
+// ahead of the SFU seed.
 __device__ __forceinline__ uint32_t top_phase(const uint4& A, uint32_t k) {
-    const uint64_t u = ((uint64_t)A.y << 32) | A.x;
-    const uint64_t v = ((uint64_t)A.w << 32) | A.z;
-    return (uint32_t)((v + (uint64_t)k * u) >> 32);
+    return __umulhi(k, A.x) + k * A.y + A.w;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -132,6 +142,54 @@ struct Strip {
                     s = sn;
                 }
             }
+        }
+    }
+};
+
+// The three-term recurrence on the pair z_k = (cos, sin) with packed FP32x2
+// FMA.  FFMA2 has no negated addend, so the strip carries y_k = s_k z_k with
+// signs s = (+, +, -, -, +, +, ...): then z_{k+1} = 2C z_k - z_{k-1} becomes
+// y_{k+1} = (k odd ? -2C : 2C) y_k + y_{k-1}, one FFMA2 per step, and the
+// sign is folded into the data factor (x or -x) of the pair sums.  Each lane
+// rounds exactly as the scalar form does (round to nearest is symmetric), so
+// the sums are bit-identical to Strip<F, kRecur3>.  Per term: 1 FFMA2 for the
+// recurrence, 1 FFMA2 for (XC, XS), 2 FFMA for CC, CS -- 4 issue slots for
+// the same 6 FMA-pipe lane operations.
+template <int F>
+struct Strip<F, kRecur3x2> {
+    float xc[F], xs[F], cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) xc[i] = xs[i] = cc[i] = cs[i] = 0.f;
+    }
+
+    __device__ __forceinline__ void acc(int i, float2 xf, float2 y) {
+        const float2 a = __ffma2_rn(xf, y, make_float2(xc[i], xs[i]));
+        xc[i] = a.x;
+        xs[i] = a.y;
+        cc[i] = fmaf(y.x, y.x, cc[i]);
+        cs[i] = fmaf(y.x, y.y, cs[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, uint32_t k0) {
+        const uint32_t p = top_phase(A, k0);
+        const float C = B.y, S = B.z, C2 = 2.f * B.y;
+        float s, c;
+        __sincosf(phase_to_angle(p), &s, &c);
+        const float2 xp = make_float2(x, x), xn = make_float2(-x, -x);
+        const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
+        float2 y0 = make_float2(c, s);
+        acc(0, xp, y0);
+        if (F == 1) return;
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, xp, y1);
+#pragma unroll
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            acc(i, ((i >> 1) & 1) ? xn : xp, y2);
+            y0 = y1;
+            y1 = y2;
         }
     }
 };

@@ -32,6 +32,8 @@
 //             identity, z_{k+1} = 2 cos(2 pi u_j) z_k - z_{k-1}: 2 FMA-pipe ops
 //             per term.  Its rounding error grows like F^2 ulp, and like
 //             F ulp / sin(2 pi u_j) for samples whose step angle is near 0 or pi.
+//   RECUR3 x2 -- the same arithmetic with the (cos, sin) pair in packed FP32x2
+//             FMA (FFMA2): fewer issue slots per term, bit-identical sums.
 // NAIVE_FP32 -- the paper's own single-precision phase f*t - rintf(f*t)
 //             (Sec. 4.3), kept as a comparator.
 #include "ls_device.cuh"
@@ -183,6 +185,7 @@ MainFn main_fn(int mode, int F) {
         case kMufu: return main_fn_f<kMufu>(F);
         case kRecur: return main_fn_f<kRecur>(F);
         case kRecur3: return main_fn_f<kRecur3>(F);
+        case kRecur3x2: return main_fn_f<kRecur3x2>(F);
         default: return nullptr;
     }
 }

@@ -18,7 +18,7 @@ using namespace lsp::host;
 namespace {
 
 lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
-    if (o->sincos_mode < 0 || o->sincos_mode > 3)
+    if (o->sincos_mode < 0 || o->sincos_mode > 4)
         return fail(ctx, LSP_ERR_INVALID_ARG, "sincos_mode %d out of range", o->sincos_mode);
     if (o->phase_mode < 0 || o->phase_mode > 1)
         return fail(ctx, LSP_ERR_INVALID_ARG, "phase_mode %d out of range", o->phase_mode);
@@ -62,17 +62,26 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     } else if (o.sincos_mode == LSP_SINCOS_RECUR) {
         s.mode = lsp::kModeRecur;
         s.F = 16;
+    } else if (o.sincos_mode == LSP_SINCOS_RECUR3_X2) {
+        s.mode = lsp::kModeRecur3x2;
+        s.F = 24;
     } else {
         s.mode = lsp::kModeRecur3;
         s.F = 24;
     }
     if (o.freqs_per_thread) s.F = o.freqs_per_thread;
+    finish_shape(ctx, s, lsp::main_occupancy(s.mode, s.F), N, N_f, o.split);
+    return s;
+}
+
+// Frequency blocks, padding and the N_t split of a shape whose mode and F are
+// set; occ = resident CTAs per SM of its kernel.
+void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64_t N, int64_t N_f, int split) {
     const int64_t per_block = lsp::freqs_per_block(s.F);
     s.nfb = (int)((N_f + per_block - 1) / per_block);
     s.nf_pad = (int64_t)s.nfb * per_block;
-    int split = o.split;
     if (split <= 0) {
-        const int occ = std::max(1, lsp::main_occupancy(s.mode, s.F));
+        const int occ = std::max(1, occ_in);
         const int64_t slots = (int64_t)occ * std::max(1, ctx->sms);
         const int64_t max_split = std::max<int64_t>(1, N / lsp::kTile);
         double best = -1.0;
@@ -92,7 +101,6 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     if (split > N) split = (int)std::max<int64_t>(1, N);
     s.chunk = (N + split - 1) / split;
     s.split = (int)((N + s.chunk - 1) / s.chunk);
-    return s;
 }
 
 extern "C" {
@@ -263,6 +271,7 @@ lsp_status lsp_sync(lsp_ctx* ctx, double timeout_s) {
         LSP_CUDA(ctx, cudaMemsetAsync(ctx->status_d, 0, sizeof(int), ctx->stream));
         LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (flags & lsp::kStatusNonFinite) return fail(ctx, LSP_ERR_NONFINITE, "non-finite value in t or X");
+        if (flags & lsp::kStatusBadWeight) return fail(ctx, LSP_ERR_INVALID_ARG, "dy must be finite and > 0");
         return fail(ctx, LSP_ERR_DEGENERATE, "X has zero variance");
     }
     return LSP_OK;
@@ -291,7 +300,8 @@ void lsp_destroy(lsp_ctx* ctx) {
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_plan(ctx);
-    DevBuf* bufs[] = {&ctx->recA,   &ctx->recB,   &ctx->recN,   &ctx->part,    &ctx->stats,  &ctx->t_stage,
+    DevBuf* bufs[] = {&ctx->recQ,   &ctx->dy_stage,
+                      &ctx->recA,   &ctx->recB,   &ctx->recN,   &ctx->part,    &ctx->stats,  &ctx->t_stage,
                       &ctx->x_stage, &ctx->p_stage, &ctx->stat_parts, &ctx->stat_counters, &ctx->b_recA,
                       &ctx->b_recB,  &ctx->b_xr,   &ctx->b_stats, &ctx->b_items, &ctx->b_head, &ctx->b_maxkey,
                       &ctx->b_seed,  &ctx->b_off,  &ctx->b_nf,   &ctx->b_f0,    &ctx->b_df,   &ctx->b_poff,

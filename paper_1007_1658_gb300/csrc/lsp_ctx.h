@@ -63,6 +63,7 @@ struct lsp_ctx {
     int sms = 0;
     // single-curve workspace
     lsp::host::DevBuf recA, recB, recN, part, stats, t_stage, x_stage, p_stage, stat_parts, stat_counters;
+    lsp::host::DevBuf recQ, dy_stage;  // floating-mean periodogram: sqrt(w_j), staged errors
     // batch workspace
     lsp::host::DevBuf b_recA, b_recB, b_xr, b_stats, b_items, b_head, b_maxkey, b_seed, b_off, b_nf, b_f0,
         b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax;
@@ -208,6 +209,10 @@ inline lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf,
 
 // Launch shape of the single-curve path for the context's options.
 lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
+
+// Frequency blocks, padding and N_t split (split <= 0: fill whole waves of
+// occ resident CTAs per SM) of a shape whose mode and F are already set.
+void finish_shape(const lsp_ctx* ctx, lsp::MainShape& s, int occ, int64_t N, int64_t N_f, int split);
 
 // Autotuned entry for this size bucket, or null.
 const TuneEntry* tuned(const lsp_ctx* ctx, int64_t N, int64_t N_f);

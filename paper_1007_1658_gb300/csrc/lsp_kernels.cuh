@@ -11,14 +11,15 @@ namespace lsp {
 enum : int {
     kStatusNonFinite = 1,
     kStatusDegenerate = 2,
+    kStatusBadWeight = 4,   // a per-sample error that is not finite and > 0
 };
 
 // Per-curve statistics written by prep_stats (Sec. 3 normalization, FP64).
 struct CurveStats {
-    double mean;     // mean of X
+    double mean;     // mean of X (weighted with 1/dy^2 when errors are given)
     double inv_sd;   // 1/sqrt(population variance); NaN when degenerate
     double t_ref;    // earliest sample time (phase origin)
-    double pad;
+    double pad;      // the variance; with errors, the weight sum sum 1/dy^2
 };
 
 // Phase records of one sample, 32 bytes, consumed by the main kernels.
@@ -26,8 +27,9 @@ struct CurveStats {
 //       both as 64-bit fixed-point turns (t' = t - t_ref).
 //   B = {x_hat, cos 2 pi u, sin 2 pi u, bits of round(u / 2^32)}.
 // The offsets folded into v: 2^63 (half a turn, so that the bit-trick angle
-// below lands on the true phase), 2^31 (round the top word) and 2^40 (round
-// the 23-bit mantissa taken from the top word).
+// below lands on the true phase), 2^31 (round the top word, for readers of
+// the full 64-bit phase) and 2^40 (round the 23-bit mantissa taken from the
+// top word).
 constexpr uint64_t kPhaseOffset = (1ull << 63) + (1ull << 40) + (1ull << 31);
 
 // Per-slice partial statistics when several CTAs share one curve.
@@ -46,19 +48,26 @@ int prep_stats_slices(int n_curves, int64_t n0);
 // Kernel launchers (all asynchronous on `st`).
 // Curves are given in CSR form: samples of curve c are [off[c], off[c+1]).
 // When off == nullptr there is one curve of n0 samples.
+// dy (optional, floating-mean periodogram): per-sample errors, weights 1/dy^2.
 cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
                               int n_curves, CurveStats* stats, int* status, StatPart* parts,
-                              unsigned* counters, cudaStream_t st);
+                              unsigned* counters, cudaStream_t st, const double* dy = nullptr);
 
 // X may be null (noise batches): then only t_ref is computed and x_hat = 0.
 // xout, if given, receives x_hat as a plain FP32 array (batch layout).
+// qout (floating-mean periodogram, stats from launch_prep_stats with the same
+// dy, or none for equal weights) receives q_j = sqrt(w_j), sum w = 1, and x_hat
+// becomes q_j (X_j - mean_w) / sd_w.
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
-                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st);
+                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st,
+                                const double* dy = nullptr, float* qout = nullptr);
 
 // Kernel modes (how sin/cos and the phase are formed in the O(N_t N_f) loop).
-enum : int { kModeMufu = 1, kModeRecur = 2, kModeNaive = 3, kModeRecur3 = 4 };
+// kModeRecur3x2 is RECUR3 with the (cos, sin) pair carried through packed
+// FP32x2 FMA (FFMA2); its results are bit-identical to kModeRecur3.
+enum : int { kModeMufu = 1, kModeRecur = 2, kModeNaive = 3, kModeRecur3 = 4, kModeRecur3x2 = 5 };
 
 struct MainShape {
     int mode;      // kMode*
@@ -84,6 +93,17 @@ cudaError_t launch_main(const MainShape& s, const uint4* recA, const float4* rec
 
 cudaError_t launch_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f,
                             float* P_out, cudaStream_t st);
+
+// ---- floating-mean periodogram (gls.cu) ----
+
+// Six partial-sum rows per chunk (XC, XS, C, S, CC', CS'); q holds sqrt(w_j).
+// Strip lengths 8 and 16; modes MUFU, RECUR, RECUR3.
+constexpr int kGlsRows = 6;
+int gls_occupancy(int mode, int F);
+cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB, const float* q, int64_t N,
+                       int64_t N_f, float* part, float* P_out, cudaStream_t st);
+cudaError_t launch_gls_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f, float* P_out,
+                                cudaStream_t st);
 
 // ---- batched evaluation (batch.cu) and noise (noise.cu) ----
 

@@ -58,10 +58,15 @@ __device__ double block_min(double v, double* sh) {
 // (Chan, Golub & LeVeque's pairwise update), so the result does not depend
 // on which CTA finishes last.  A degenerate curve gets inv_sd = NaN, so its
 // periodogram comes out NaN and the status word says why.
+// With per-sample errors dy (floating-mean periodogram) every sample carries
+// the weight v = 1/dy^2: the mean and variance are the weighted ones, n
+// becomes the weight sum, and a dy that is not finite and > 0 is flagged.
+// Without dy every weight is 1 and the arithmetic is the unweighted one.
 __global__ void __launch_bounds__(kStatsThreads)
 prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
                   const int64_t* __restrict__ off, int64_t n0, CurveStats* __restrict__ stats,
-                  int* __restrict__ status, StatPart* __restrict__ parts, unsigned* __restrict__ counters) {
+                  int* __restrict__ status, StatPart* __restrict__ parts, unsigned* __restrict__ counters,
+                  const double* __restrict__ dy) {
     __shared__ double sh[33];
     __shared__ int last;
     const int c = blockIdx.y, g = blockIdx.x, G = gridDim.x;
@@ -71,27 +76,42 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
     const int64_t L = (n + G - 1) / G;
     const int64_t sb = min(e, b + (int64_t)g * L);
     const int64_t se = min(e, sb + L);
-    double s = 0.0, tmin = DBL_MAX;
-    int bad = 0;
+    double s = 0.0, tmin = DBL_MAX, ws = 0.0;
+    int bad = 0, badw = 0;
     for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
         const double x = X ? X[j] : 0.0, tj = t[j];
         bad |= !(isfinite(x) && isfinite(tj));
-        s += x;
+        if (dy) {
+            const double ej = dy[j];
+            const double wj = 1.0 / (ej * ej);
+            badw |= !(isfinite(ej) && ej > 0.0 && isfinite(wj) && wj > 0.0);
+            ws += wj;
+            s += wj * x;
+        } else {
+            s += x;
+        }
         tmin = fmin(tmin, tj);
     }
     bad = __syncthreads_or(bad);
+    badw = __syncthreads_or(badw);
     s = block_sum(s, sh);
     tmin = block_min(tmin, sh);
-    const double cnt = (double)(se - sb);
+    const double cnt = dy ? block_sum(ws, sh) : (double)(se - sb);
     const double mean_g = cnt > 0 ? s / cnt : 0.0;
     double v = 0.0;
     if (X) {
         for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
             const double d = X[j] - mean_g;
-            v = fma(d, d, v);
+            if (dy) {
+                const double ej = dy[j];
+                v = fma(d / (ej * ej), d, v);
+            } else {
+                v = fma(d, d, v);
+            }
         }
     }
     v = block_sum(v, sh);
+    bad |= badw << 1;  // bit 1: bad weight
     double tot_n = cnt, mean = mean_g, m2 = v;
     if (G > 1) {
         if (threadIdx.x == 0) {
@@ -131,15 +151,16 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
     }
     if (threadIdx.x == 0) {
         // without X (noise drawn later) only t_ref matters: unit scale
-        const double var = X ? m2 / (double)n : 1.0;
+        const double var = X ? m2 / (dy ? tot_n : (double)n) : 1.0;
         const bool ok = !bad && var > 0.0 && n >= 2;
         CurveStats r;
         r.mean = mean;
         r.inv_sd = ok ? 1.0 / sqrt(var) : __longlong_as_double(0x7ff8000000000000ll);
         r.t_ref = bad ? 0.0 : tmin;
-        r.pad = var;
+        r.pad = dy ? tot_n : var;
         stats[c] = r;
-        if (bad) atomicOr(status, kStatusNonFinite);
+        if (bad & 1) atomicOr(status, kStatusNonFinite);
+        else if (bad) atomicOr(status, kStatusBadWeight);
         else if (!ok) atomicOr(status, kStatusDegenerate);
     }
 }
@@ -163,7 +184,7 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
                     const double* __restrict__ f0a, const double* __restrict__ dfa,
                     double f0s, double dfs, const CurveStats* __restrict__ stats,
                     uint4* __restrict__ recA, float4* __restrict__ recB, float2* __restrict__ recN,
-                    float* __restrict__ xout) {
+                    float* __restrict__ xout, const double* __restrict__ dy, float* __restrict__ qout) {
     const int c = blockIdx.y;
     const int64_t b = off ? off[c] : 0;
     const int64_t e = off ? off[c + 1] : n0;
@@ -180,7 +201,16 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
         const double turn = (double)(int64_t)u * 0x1p-64;
         double sn, cs;
         sincospi(2.0 * turn, &sn, &cs);
-        const float xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
+        float xh;
+        if (qout) {
+            // floating-mean form: q = sqrt(w_j) with w_j = v_j / sum v (sum w = 1;
+            // equal weights without dy), x = q (X - mean_w) / sd_w, so sum x^2 = 1
+            const double q = dy ? rsqrt(st.pad) / dy[j] : rsqrt((double)(e - b));
+            qout[j] = (float)q;
+            xh = (float)((X[j] - st.mean) * st.inv_sd * q);
+        } else {
+            xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
+        }
         recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
         recB[j] = make_float4(xh, (float)cs, (float)sn, __uint_as_float(du));
         if (recN) recN[j] = make_float2(xh, __double2float_rn(tt));
@@ -198,24 +228,25 @@ int prep_stats_slices(int n_curves, int64_t n0) {
 
 cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* off, int64_t n0,
                               int n_curves, CurveStats* stats, int* status, StatPart* parts,
-                              unsigned* counters, cudaStream_t st) {
+                              unsigned* counters, cudaStream_t st, const double* dy) {
     // without slice scratch every curve gets one CTA
     const int G = (parts && counters) ? prep_stats_slices(n_curves, n0) : 1;
     dim3 grid((unsigned)G, (unsigned)n_curves);
-    prep_stats_kernel<<<grid, kStatsThreads, 0, st>>>(t, X, off, n0, stats, status, parts, counters);
+    prep_stats_kernel<<<grid, kStatsThreads, 0, st>>>(t, X, off, n0, stats, status, parts, counters, dy);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
-                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st) {
+                                uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st,
+                                const double* dy, float* qout) {
     int64_t bx = (max_n + 255) / 256;
     if (bx > 4096) bx = 4096;
     if (bx < 1) bx = 1;
     dim3 grid((unsigned)bx, (unsigned)n_curves);
     prep_records_kernel<<<grid, 256, 0, st>>>(t, X, off, n0, f0, df, f0_single, df_single, stats,
-                                              recA, recB, recN, xout);
+                                              recA, recB, recN, xout, dy, qout);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ _lock = threading.Lock()
 
 OK, ERR_INVALID_ARG, ERR_DEGENERATE, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_MODEL, \
     ERR_UNSUPPORTED = range(9)
-SINCOS_AUTO, SINCOS_MUFU, SINCOS_RECUR, SINCOS_RECUR3 = 0, 1, 2, 3
+SINCOS_AUTO, SINCOS_MUFU, SINCOS_RECUR, SINCOS_RECUR3, SINCOS_RECUR3_X2 = 0, 1, 2, 3, 4
 PHASE_FIXED64, PHASE_NAIVE_FP32 = 0, 1
 
 _NAMES = {0: "OK", 1: "INVALID_ARG", 2: "DEGENERATE", 3: "NONFINITE", 4: "OOM", 5: "CUDA",
@@ -59,6 +59,7 @@ def load():
         lib.lsp_set_options.argtypes = [p, ctypes.POINTER(lsp_options)]
         lib.lsp_set_stream.argtypes = [p, p]
         lib.lsp_periodogram.argtypes = [p, p, p, i64, d, d, i64, p]
+        lib.lsp_periodogram_gls.argtypes = [p, p, p, p, i64, d, d, i64, p]
         lib.lsp_grid.argtypes = [d, d, i64, d, d, p, p, p]
         lib.lsp_sync.argtypes = [p, d]
         lib.lsp_last_timing.argtypes = [p, p, p, p]
@@ -193,6 +194,22 @@ class Context:
         n = t.numel() if hasattr(t, "numel") else t.size
         self._check(self._lib.lsp_periodogram(self.h, _ptr(t), _ptr(X), int(n), float(f0), float(df), nf,
                                               _ptr(out)))
+        return out
+
+    def periodogram_gls(self, t, X, f0, df, nf, dy=None, out=None):
+        """Floating-mean periodogram, P[k] = (N_t/2) p(f0 + k df) with weights 1/dy^2
+        (equal weights when dy is None); lsp_periodogram_gls."""
+        nf = int(nf)
+        if out is None:
+            if hasattr(t, "data_ptr"):
+                import torch
+                out = torch.empty(nf, dtype=torch.float32, device=t.device)
+            else:
+                out = np.empty(nf, dtype=np.float32)
+        self._bind_stream()
+        n = t.numel() if hasattr(t, "numel") else t.size
+        self._check(self._lib.lsp_periodogram_gls(self.h, _ptr(t), _ptr(X), _ptr(dy), int(n), float(f0), float(df),
+                                                  nf, _ptr(out)))
         return out
 
     def batch(self, t_off, t, f0, df, nf, X=None, seed=0, n_real=1, P_out=None, P_off=None,

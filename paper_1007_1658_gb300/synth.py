@@ -16,6 +16,18 @@ Workloads (sizes as named by each function):
   7,282 dropped at random (first and last kept) -> 65,536 samples; two
   1e-3-amplitude sinusoids near 20 c/d + N(0, 1e-3); oversampling 10 up to
   24.5 c/d (318,500 bins).
+* ``corot_382k``      -- the shape of the paper's benchmark light curve (a
+  150-d space-photometry run, 382,003 samples at a nominal 32-s cadence, Sec.
+  5.2): 32-s slots over 150 d with +-0.5-s timing jitter, runs of 8-16 slots
+  dropped once per 103-min orbit in 80% of the orbits (trimmed to exactly
+  382,003 samples), a beta-Cephei-like signal (dominant 5.49 c/d = 0.18-d mode,
+  amplitude 1e-2, four weaker modes in 4-13 c/d) + N(0, 1e-3) noise + a slow
+  drift; grid df = f_0 = 1/(4T), N_f = 1,528,064 (oversampling 4 to twice the
+  mean Nyquist frequency, rounded up to a multiple of 256).  ``step`` > 1 keeps
+  every step-th sample (uniform down-sampling) and scales N_f with N_t.
+* ``with_errors``     -- per-sample errors for the floating-mean periodogram:
+  dy log-uniform in [0.3, 3] x ``sigma``, 2% of the samples 10x noisier; the
+  curve's values plus a constant ``offset`` plus dy_j N(0, 1).
 * ``noise_batch``     -- sampling patterns for Monte-Carlo: N_t log-uniform
   in [200, 20000], span T log-uniform in [30, 1000] d, nightly windows and
   seasonal gaps, grid oversampling 4 up to the mean Nyquist frequency.
@@ -93,6 +105,56 @@ def cadence_65k(seed: int = SEED_BASE + 3, slots: int = 72_818, keep: int = 65_5
     df = 1.0 / (f_over * _span(t))
     nf = int(round(f_max / df))
     return Curve(t, X, df, df, nf, sig)
+
+
+def corot_382k(seed: int = SEED_BASE + 6, step: int = 1) -> Curve:
+    rng = np.random.default_rng(seed)
+    cad = 32.0 / 86400.0                      # 32 s in days
+    span = 150.0
+    slots = int(span / cad)                   # 405,000
+    keep_n = 382_003
+    orbit = 103.0 / 1440.0
+    per_orbit = orbit / cad
+    drop = np.zeros(slots, dtype=bool)
+    for o in range(int(span / orbit) + 1):
+        if rng.random() < 0.8:
+            start = int(o * per_orbit + rng.uniform(0, per_orbit))
+            drop[start:start + int(rng.integers(8, 17))] = True
+    kept = np.flatnonzero(~drop[:slots])
+    if kept.size > keep_n:  # trim at random to the exact count (first and last kept)
+        inner = rng.choice(kept[1:-1], size=keep_n - 2, replace=False)
+        kept = np.sort(np.concatenate([[kept[0], kept[-1]], inner]))
+    t = kept * cad + rng.uniform(-0.5, 0.5, kept.size) / 86400.0
+    t = np.sort(t)
+    freqs = (5.4869, 5.9173, 4.3716, 7.9342, 12.8127)
+    amps = (1e-2, 2.1e-3, 1.2e-3, 6e-4, 3e-4)
+    phases = rng.uniform(0, 2 * np.pi, len(freqs))
+    X = 1.0 + 2e-3 * (t / span) ** 2 + rng.normal(0.0, 1e-3, t.size)
+    for f, a, p in zip(freqs, amps, phases):
+        X += a * np.sin(2 * np.pi * f * t + p)
+    if step > 1:
+        t, X = t[::step], X[::step]
+    df = 1.0 / (4.0 * _span(t))
+    nf = int(-(-(4 * t.size) // 256) * 256)  # F_over F_high N_t / 2 with F_over F_high = 8
+    return Curve(t, X, df, df, nf, freqs)
+
+
+@dataclass
+class ErrCurve(Curve):
+    dy: np.ndarray = None  # float64 [N_t], per-sample 1-sigma errors
+
+
+def with_errors(make, seed: int = SEED_BASE + 5, sigma: float = 0.5, offset: float = 12.0, **kw) -> ErrCurve:
+    """Curve `make(**kw)` with per-sample errors: dy_j log-uniform in
+    [0.3, 3] sigma, 2% of the samples 10x noisier; X = the curve's own values
+    + offset + dy_j N(0, 1)."""
+    c = make(**kw)
+    rng = np.random.default_rng(seed)
+    n = c.t.size
+    dy = sigma * np.exp(rng.uniform(np.log(0.3), np.log(3.0), n))
+    dy[rng.random(n) < 0.02] *= 10.0
+    X = c.X + offset + dy * rng.normal(0.0, 1.0, n)
+    return ErrCurve(c.t, X, c.f0, c.df, c.nf, c.signal_freqs, dy)
 
 
 def pattern_times(rng, n: int, T: float) -> np.ndarray:

@@ -34,7 +34,8 @@ def lib():
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ("lsp_create", "lsp_periodogram", "lsp_batch", "lsp_fap_predict", "lsp_destroy", "lsp_sync",
-                 "lsp_grid", "lsp_last_error", "lsp_noise", "lsp_fap_train_step", "lsp_periodogram_noalloc"):
+                 "lsp_grid", "lsp_last_error", "lsp_noise", "lsp_fap_train_step", "lsp_periodogram_noalloc",
+                 "lsp_periodogram_gls"):
         assert must in names, must
 
 

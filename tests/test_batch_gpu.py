@@ -63,7 +63,7 @@ def _oracle_noise_curve(b, seed, c, r):
     return t, X
 
 
-@pytest.mark.parametrize("mode", [3, 2, 1])
+@pytest.mark.parametrize("mode", [4, 3, 2, 1])
 def test_noise_batch_matches_oracle(ctx, lsp, mode):
     b = _small_batch()
     seed, n_real = 99, 3

@@ -45,7 +45,7 @@ def _run(ctx, t, X, f0, df, nf, **opts):
     return P.cpu().numpy().astype(np.float64)
 
 
-MODES = [dict(sincos_mode=2), dict(sincos_mode=1), dict(sincos_mode=3)]
+MODES = [dict(sincos_mode=2), dict(sincos_mode=1), dict(sincos_mode=3), dict(sincos_mode=4)]
 
 
 @pytest.mark.parametrize("opts", MODES + [dict(sincos_mode=2, freqs_per_thread=4),
@@ -68,7 +68,7 @@ def test_plain_1k_full_grid(ctx, opts):
 
 @pytest.mark.parametrize("n,nf", [(2, 7), (3, 1), (5, 64), (255, 511), (256, 512), (257, 513),
                                   (1000, 2049), (4099, 2048), (1023, 4097), (600, 1)])
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_ragged_sizes(ctx, n, nf, mode):
     rng = np.random.default_rng(n * 7919 + nf)
     t = np.sort(rng.uniform(0, 37.0, n))
@@ -305,3 +305,17 @@ def test_even_grid_noise_maxima_follow_the_exact_dirichlet_law(ctx):
     for p in (0.5, 0.9, 0.99):
         Q = oracle.fap(srt[int(np.ceil(p * R)) - 1], N, nf)
         assert abs((1 - Q) - p) < 0.08, (p, Q)
+
+
+@pytest.mark.parametrize("F", [8, 16, 24, 28])
+def test_packed_recurrence_is_bit_identical_to_scalar(ctx, F):
+    """RECUR3_X2 carries (cos, sin) through packed FP32x2 FMA with sign-folded
+    steps; every lane must round exactly as the scalar three-term form does."""
+    from paper_1007_1658_gb300 import synth
+    c = synth.gapped_100k()
+    nf = 40_000
+    outs = []
+    for mode in (3, 4):
+        for split in (1, 6):
+            outs.append(_run(ctx, c.t, c.X, c.f0, c.df, nf, sincos_mode=mode, freqs_per_thread=F, split=split))
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
