@@ -56,7 +56,7 @@ struct GStrip {
     }
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
-        uint32_t p = top_phase(A, k0);
+        uint32_t p = top_phase_hi(A, k0);
         if (MODE == kMufu) {
             const uint32_t du = __float_as_uint(B.w);
 #pragma unroll
@@ -119,7 +119,7 @@ struct GStrip<F, kRecur3x2> {
     }
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
-        const uint32_t p = top_phase(A, k0);
+        const uint32_t p = top_phase_hi(A, k0);
         const float C = B.y, S = B.z, C2 = 2.f * B.y;
         float s, c;
         __sincosf(phase_to_angle(p), &s, &c);

@@ -30,14 +30,20 @@ __device__ __forceinline__ float phase_to_angle(uint32_t p) {
     return fmaf(__uint_as_float(0x3F800000u | (p >> 9)), kTwoPi, -kThreePi);
 }
 
-// Top 32 bits of the phase v + k u (mod 2^64) of record A at frequency k,
-// from 32-bit products: v_hi + k u_hi + hi(k u_lo).  The carry of the low
-// word (v_lo + lo(k u_lo)) is left out, so the result is the exact top word
-// or one less: an error below 2^-32 turn, far under the 2^-23-turn step of
-// the FP32 angle taken from it (the 2^40 rounding offset in v sits in the top
-// word and still rounds that step).  A short dependency chain (two IMAD)
-// ahead of the SFU seed.
+// Top 32 bits of the phase v + k u (mod 2^64) of record A at frequency k.
 __device__ __forceinline__ uint32_t top_phase(const uint4& A, uint32_t k) {
+    const uint64_t u = ((uint64_t)A.y << 32) | A.x;
+    const uint64_t v = ((uint64_t)A.w << 32) | A.z;
+    return (uint32_t)((v + (uint64_t)k * u) >> 32);
+}
+
+// The same word from 32-bit products only: v_hi + k u_hi + hi(k u_lo).  The
+// carry of the low word (v_lo + lo(k u_lo)) is left out, so the result is the
+// exact top word or one less: an error below 2^-32 turn, far under the
+// 2^-23-turn step of the FP32 angle taken from it (the 2^40 rounding offset
+// in v sits in the top word and still rounds that step).  Measured faster in
+// the six-sum floating-mean strips, slower in the four-sum ones.
+__device__ __forceinline__ uint32_t top_phase_hi(const uint4& A, uint32_t k) {
     return __umulhi(k, A.x) + k * A.y + A.w;
 }
 

@@ -27,9 +27,8 @@ struct CurveStats {
 //       both as 64-bit fixed-point turns (t' = t - t_ref).
 //   B = {x_hat, cos 2 pi u, sin 2 pi u, bits of round(u / 2^32)}.
 // The offsets folded into v: 2^63 (half a turn, so that the bit-trick angle
-// below lands on the true phase), 2^31 (round the top word, for readers of
-// the full 64-bit phase) and 2^40 (round the 23-bit mantissa taken from the
-// top word).
+// below lands on the true phase), 2^31 (round the top word) and 2^40 (round
+// the 23-bit mantissa taken from the top word).
 constexpr uint64_t kPhaseOffset = (1ull << 63) + (1ull << 40) + (1ull << 31);
 
 // Per-slice partial statistics when several CTAs share one curve.
