@@ -345,6 +345,13 @@ def run_paper_shape(torch, dev, stream, args, peaks, sms):
                 row["cpu_oracle_ms"] = 1e3 * (time.perf_counter() - t0)
             sweep.append(row)
         ctx.sync(120.0)
+        # Press-Rybicki approximation of the full-size curve (the last one above)
+        fn = lambda: ctx.press_rybicki(t_d, X_d, c.f0, c.df, c.nf, macc=4, out=Q_d)
+        Q_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
+        pr_ms = _time_calls(torch, stream, fn, 2, 3, flush)
+        pr_launches = ctx.last_launch_count()
+        ctx.sync(120.0)
+        pr_err = float((Q_d - P_d).abs().max() / P_d.max())
     ctx.close()
     full = sweep[-1]
     big = sweep[-4:]
@@ -354,7 +361,11 @@ def run_paper_shape(torch, dev, stream, args, peaks, sms):
                         "f_0 = df = 1/(4T); sweep by uniform down-sampling",
             "t_calc_s": full["gpu_ms"] * 1e-3, "terms_per_s": full["gpu_terms_per_s"],
             "paper_c1060_t_calc_s": 20.3, "paper_8core_cpu_t_calc_s": 566.0,
-            "slope_dlog_t_dlog_Nt_top4": slope, "sweep": sweep,
+            "slope_dlog_t_dlog_Nt_top4": slope,
+            "press_rybicki": {"macc": 4, "ms": pr_ms, "launches": pr_launches,
+                              "speedup_vs_exact": full["gpu_ms"] / pr_ms,
+                              "max_abs_dP_over_maxP_vs_exact": pr_err},
+            "sweep": sweep,
             "cpu_cores": oracle.num_threads() if args.cpu_baseline else None, "clocks": clk.summary()}
 
 

@@ -143,6 +143,24 @@ lsp_status lsp_periodogram_gls(lsp_ctx *ctx, const double *t, const double *X, c
                                int64_t N_t, double f_0, double df, int64_t N_f, float *P_out);
 
 /*
+ * Fast approximate P_n by the method of Press & Rybicki (1989), which the
+ * paper's introduction cites as the O(N log N) alternative to the direct
+ * evaluation: the normalized data are spread ("extirpolated") onto a uniform
+ * periodic grid of n_fft = 2^p >= 2 macc (f_0/df + N_f) nodes spanning 1/df
+ * with macc-point Lagrange weights (and unit values at the positions of
+ * 2(t - t0) for the tau sums), one FFT gives the sums of Eq. 5-8 at every
+ * multiple of df, and Eq. 5-6 follow.  Same arguments as lsp_periodogram plus
+ * macc (even, 2..16; 0 = 4).  f_0 must be a non-negative integer multiple of
+ * df (the grid of Eq. 9 is: f_0 = df).  Accuracy: the extirpolation error,
+ * about 1e-4 max P at macc = 4 and falling fast with macc; exact when every
+ * sample sits on a grid node.  Workspace: 32 n_fft bytes (n_fft <= 2^28).
+ * Errors: INVALID_ARG (also f_0 not on the FFT grid, bad macc, grid too
+ * large), NONFINITE, DEGENERATE, OOM, CUDA.
+ */
+lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int64_t N_t, double f_0,
+                             double df, int64_t N_f, int32_t macc, float *P_out);
+
+/*
  * Many periodograms in one call: measured curves, or Monte-Carlo noise
  * realizations of sampling patterns (Sec. 6.2: the distribution of peak
  * heights under pure noise, e.g. the number of independent frequencies that

@@ -300,7 +300,7 @@ void lsp_destroy(lsp_ctx* ctx) {
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_plan(ctx);
-    DevBuf* bufs[] = {&ctx->recQ,   &ctx->dy_stage,
+    DevBuf* bufs[] = {&ctx->recQ,   &ctx->dy_stage, &ctx->pr_acc, &ctx->pr_z0, &ctx->pr_z1,
                       &ctx->recA,   &ctx->recB,   &ctx->recN,   &ctx->part,    &ctx->stats,  &ctx->t_stage,
                       &ctx->x_stage, &ctx->p_stage, &ctx->stat_parts, &ctx->stat_counters, &ctx->b_recA,
                       &ctx->b_recB,  &ctx->b_xr,   &ctx->b_stats, &ctx->b_items, &ctx->b_head, &ctx->b_maxkey,

@@ -64,6 +64,7 @@ struct lsp_ctx {
     // single-curve workspace
     lsp::host::DevBuf recA, recB, recN, part, stats, t_stage, x_stage, p_stage, stat_parts, stat_counters;
     lsp::host::DevBuf recQ, dy_stage;  // floating-mean periodogram: sqrt(w_j), staged errors
+    lsp::host::DevBuf pr_acc, pr_z0, pr_z1;  // Press-Rybicki: FP64 grid, FFT ping-pong buffers
     // batch workspace
     lsp::host::DevBuf b_recA, b_recB, b_xr, b_stats, b_items, b_head, b_maxkey, b_seed, b_off, b_nf, b_f0,
         b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax;

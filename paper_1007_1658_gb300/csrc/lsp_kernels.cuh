@@ -104,6 +104,16 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
 cudaError_t launch_gls_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f, float* P_out,
                                 cudaStream_t st);
 
+// ---- Press-Rybicki fast approximation (press_rybicki.cu) ----
+
+// FFT grid size: the smallest power of two >= 2 macc (k_hi + 1).
+int64_t pr_fft_size(int64_t k_hi, int macc);
+// Extirpolation onto n_fft nodes (acc: FP64 grid, zeroed here), FFT (z0/z1
+// ping-pong), P at bins j0 .. j0+N_f-1 into P_out.  *launches: kernels run.
+cudaError_t launch_pr(const double* t, const double* X, int64_t N, const CurveStats* stats, double df, int64_t j0,
+                      int64_t N_f, int macc, int64_t n_fft, double2* acc, float2* z0, float2* z1, float* P_out,
+                      int* launches, cudaStream_t st);
+
 // ---- batched evaluation (batch.cu) and noise (noise.cu) ----
 
 // One work item of the persistent batch kernel: a block of kMainThreads*F

@@ -60,6 +60,7 @@ def load():
         lib.lsp_set_stream.argtypes = [p, p]
         lib.lsp_periodogram.argtypes = [p, p, p, i64, d, d, i64, p]
         lib.lsp_periodogram_gls.argtypes = [p, p, p, p, i64, d, d, i64, p]
+        lib.lsp_press_rybicki.argtypes = [p, p, p, i64, d, d, i64, i32, p]
         lib.lsp_grid.argtypes = [d, d, i64, d, d, p, p, p]
         lib.lsp_sync.argtypes = [p, d]
         lib.lsp_last_timing.argtypes = [p, p, p, p]
@@ -210,6 +211,21 @@ class Context:
         n = t.numel() if hasattr(t, "numel") else t.size
         self._check(self._lib.lsp_periodogram_gls(self.h, _ptr(t), _ptr(X), _ptr(dy), int(n), float(f0), float(df),
                                                   nf, _ptr(out)))
+        return out
+
+    def press_rybicki(self, t, X, f0, df, nf, macc=4, out=None):
+        """Press-Rybicki fast approximate P_n at f0 + k df (f0 a multiple of df)."""
+        nf = int(nf)
+        if out is None:
+            if hasattr(t, "data_ptr"):
+                import torch
+                out = torch.empty(nf, dtype=torch.float32, device=t.device)
+            else:
+                out = np.empty(nf, dtype=np.float32)
+        self._bind_stream()
+        n = t.numel() if hasattr(t, "numel") else t.size
+        self._check(self._lib.lsp_press_rybicki(self.h, _ptr(t), _ptr(X), int(n), float(f0), float(df), nf,
+                                                int(macc), _ptr(out)))
         return out
 
     def batch(self, t_off, t, f0, df, nf, X=None, seed=0, n_real=1, P_out=None, P_off=None,
