@@ -55,18 +55,22 @@ def _peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
-def _kernel_sha():
+MAIN_SOURCES = ("ls_main.cu", "ls_device.cuh", "lsp_kernels.cuh")
+GLS_SOURCES = ("gls.cu", "ls_device.cuh", "lsp_kernels.cuh")
+
+
+def _kernel_sha(files=MAIN_SOURCES):
     h = hashlib.sha256()
-    for f in ("ls_main.cu", "ls_device.cuh", "lsp_kernels.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1007_1658_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _recorded_traffic(kernel: str):
+def _recorded_traffic(kernel: str, profile="ls_main_gapped_100k.md", files=MAIN_SOURCES):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
     the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "ls_main_gapped_100k.md")
+    p = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -74,7 +78,7 @@ def _recorded_traffic(kernel: str):
     if not m:
         return None
     rec = json.loads(m.group(1))
-    if rec.get("kernel_sha") != _kernel_sha() or rec.get("kernel") != kernel:
+    if rec.get("kernel_sha") != _kernel_sha(files) or rec.get("kernel") != kernel:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -272,6 +276,7 @@ def run_gpu(args, rank, world, dist):
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(c, args.cpu_bins).items() if k != "seconds"}
     if args.batch:
         line["batched_mc"] = run_batch_bench(ctx, torch, dev, stream, args)
+        line["batched_mc"]["multi_rhs"] = run_mrhs_bench(torch, dev, stream)
     if args.gls:
         line["floating_mean"] = run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms)
     if args.paper:
@@ -412,15 +417,46 @@ def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
                                    "+ 2 FFMA), 128/clk/SM", 128.0 / 8)}[mode]
     peak = roof[1] * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
+    kernel = "gls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode])
     return {"workload": "gapped_100k with per-sample errors (dy log-U[0.15, 1.5], 2%% x10), N_t = %d, N_f = %d"
                         % (c.t.size, c.nf),
             "ms_per_call": step_ms, "terms_per_s": terms / (step_ms * 1e-3),
-            "roofline": {"bound": "alu", "kernel": "gls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode]),
+            "roofline": {"bound": "alu", "kernel": kernel,
                          "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterms/s", "frac": achieved / peak,
+                         "traffic": _recorded_traffic(kernel, "gls_main_gapped_100k_errors.md", GLS_SOURCES),
                          "peak_basis": "%s: %.2f terms/clk/SM x %d SMs x %.0f MHz (%s sm_max_mhz)" % (
                              roof[0], roof[1], sms, peaks["sm_max_mhz"], peak_src),
                          "main_ms": float(np.mean(main_ms))},
             "clocks": clk.summary()}
+
+
+def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64):
+    """Many realizations per pattern (the surrogate's training shape: 256
+    noise_batch patterns x 64 realizations, one lsp_batch call) for each
+    multi-RHS group size; every result is bit-identical across group sizes."""
+    from paper_1007_1658_gb300 import lsp, synth
+    b = synth.noise_batch(n_curves=n_patterns, seed=777001)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    off, t, f0, df, nf = d(b.t_off), d(b.t), d(b.f0), d(b.df), d(b.nf)
+    maxP = torch.empty(n_real * b.n, dtype=torch.float32, device=dev)
+    arg = torch.empty(n_real * b.n, dtype=torch.int32, device=dev)
+    out = []
+    for rhs in (1, 2, 4, 8):
+        mctx = lsp.Context(dev.index or 0, stream=stream, batch_rhs=rhs)
+        with torch.cuda.stream(stream):
+            mctx.batch(off, t, f0, df, nf, seed=1, n_real=n_real, maxP=maxP, argmax=arg)
+            mctx.sync(300.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for r in range(3):
+                mctx.batch(off, t, f0, df, nf, seed=2 + r, n_real=n_real, maxP=maxP, argmax=arg)
+            e1.record(stream)
+            mctx.sync(300.0)
+        ms = e0.elapsed_time(e1) / 3
+        mctx.close()
+        out.append({"batch_rhs": rhs, "ms": ms, "periodograms_per_s": n_real * b.n / (ms * 1e-3),
+                    "terms_per_s": n_real * b.terms / (ms * 1e-3)})
+    return {"workload": "%d noise_batch patterns x %d realizations" % (b.n, n_real), "by_group": out}
 
 
 def run_batch_bench(ctx, torch, dev, stream, args):

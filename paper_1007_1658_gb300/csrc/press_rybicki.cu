@@ -14,16 +14,38 @@
 // XC + i XS = sum x e^{i w t'} and CC - SS + 2i CS = sum e^{2 i w t'}, Eq. 5-6
 // follow in the closed form of periodogram_value.
 //
-// Kernels: spread (FP64 positions and weights, FP64 atomics into a double2
-// grid), one Stockham radix-4 pass per launch (a radix-2 pass first when
-// log2 n_fft is odd; the first pass reads the FP64 grid and rounds it to
-// FP32), and a finalize pass over the requested bins.
+// Kernels: spread (FP64 positions, FP32 Lagrange weights, FP64 atomics into a
+// double2 grid), Stockham passes of radix 16 (radix 2 and/or 4 first for the
+// remainder of log2 n_fft modulo 4; the first pass reads the FP64 grid and
+// rounds it to FP32), and a finalize pass over the requested bins.
 #include "ls_device.cuh"
 
 namespace lsp {
 namespace {
 
 constexpr int kPrThreads = 256;
+
+constexpr int kMaxMacc = 16;
+
+// Lagrange weights of the macc nodes lo .. lo+macc-1 for a position d = g - lo
+// in [macc/2 - 1, macc/2): w_i = prod_{l != i} (d - l) / prod_{l != i} (i - l),
+// numerators from prefix and suffix products, denominators 1 / (i! (macc-1-i)!)
+// with the sign (-1)^(macc-1-i).  FP32 (d is small; the FFT is FP32 too).
+__device__ __forceinline__ void lagrange_weights(float d, int macc, float* w) {
+    float pre = 1.f;
+    for (int i = 0; i < macc; ++i) {
+        w[i] = pre;
+        pre *= d - (float)i;
+    }
+    float suf = 1.f;
+    for (int i = macc - 1; i >= 0; --i) {
+        float den = 1.f;
+        for (int l = 0; l < macc; ++l)
+            if (l != i) den *= (float)(i - l);
+        w[i] *= suf / den;
+        suf *= d - (float)i;
+    }
+}
 
 __global__ void __launch_bounds__(kPrThreads)
 pr_spread_kernel(const double* __restrict__ t, const double* __restrict__ X, int64_t n,
@@ -36,19 +58,18 @@ pr_spread_kernel(const double* __restrict__ t, const double* __restrict__ X, int
         const double x = (X[j] - st.mean) * st.inv_sd;
 #pragma unroll 1
         for (int which = 0; which < 2; ++which) {
+            // position in FP64 (node choice exact), offset from the first node in FP32
             const double p = (which ? 2.0 * tt : tt) * df;
             const double g = (p - floor(p)) * nd;
             const int64_t lo = (int64_t)floor(g) - (macc / 2 - 1);
-            // Lagrange weight of node lo + i: prod_{l != i} (g - m_l) / (i - l)
+            float w[kMaxMacc];
+            lagrange_weights((float)(g - (double)lo), macc, w);
             for (int i = 0; i < macc; ++i) {
-                double w = 1.0;
-                for (int l = 0; l < macc; ++l)
-                    if (l != i) w *= (g - (double)(lo + l)) / (double)(i - l);
                 const int64_t m = (lo + i) & (n_fft - 1);  // periodic grid, n_fft a power of two
                 if (which == 0)
-                    atomicAdd(&acc[m].x, w * x);
+                    atomicAdd(&acc[m].x, (double)w[i] * x);
                 else
-                    atomicAdd(&acc[m].y, w);
+                    atomicAdd(&acc[m].y, (double)w[i]);
             }
         }
     }
@@ -122,6 +143,57 @@ fft_radix4_pass(const T* __restrict__ in, float2* __restrict__ out, int64_t n, i
     }
 }
 
+// In-place 4-point DFT with the e^{+2 pi i / 4} = i kernel.
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+    const float2 a0 = make_float2(x0.x + x2.x, x0.y + x2.y);
+    const float2 a1 = make_float2(x0.x - x2.x, x0.y - x2.y);
+    const float2 a2 = make_float2(x1.x + x3.x, x1.y + x3.y);
+    const float2 a3 = make_float2(-(x1.y - x3.y), x1.x - x3.x);
+    x0 = make_float2(a0.x + a2.x, a0.y + a2.y);
+    x1 = make_float2(a1.x + a3.x, a1.y + a3.y);
+    x2 = make_float2(a0.x - a2.x, a0.y - a2.y);
+    x3 = make_float2(a1.x - a3.x, a1.y - a3.y);
+}
+
+// One radix-16 Stockham pass (sub-transforms of length Ns become 16 Ns).  The
+// 16-point DFT runs as 4 x 4: with q = 4a + b and k = c + 4d,
+// X[c + 4d] = sum_b i^{bd} w^{bc} sum_a v[4a + b] i^{ac}, w = e^{+2 pi i / 16}.
+template <class T>
+__global__ void __launch_bounds__(kPrThreads)
+fft_radix16_pass(const T* __restrict__ in, float2* __restrict__ out, int64_t n, int64_t Ns) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f, h = 0.70710678118654752f;
+    const int64_t m = n >> 4;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = j & (Ns - 1);
+        float2 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = load_c(in, j + q * m);
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < 16; ++q) v[q] = cmul(v[q], twiddle(q * r, 16 * Ns));
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dft4(v[b], v[4 + b], v[8 + b], v[12 + b]);  // v[4c + b] = Y_b[c]
+        // inner twiddles w^{bc}
+        v[5] = cmul(v[5], make_float2(c1, s1));    // b = 1, c = 1
+        v[6] = cmul(v[6], make_float2(h, h));      // b = 2, c = 1
+        v[7] = cmul(v[7], make_float2(s1, c1));    // b = 3, c = 1
+        v[9] = cmul(v[9], make_float2(h, h));      // b = 1, c = 2
+        v[10] = make_float2(-v[10].y, v[10].x);    // b = 2, c = 2: w^4 = i
+        v[11] = cmul(v[11], make_float2(-h, h));   // b = 3, c = 2
+        v[13] = cmul(v[13], make_float2(s1, c1));  // b = 1, c = 3
+        v[14] = cmul(v[14], make_float2(-h, h));   // b = 2, c = 3
+        v[15] = cmul(v[15], make_float2(-c1, -s1));  // b = 3, c = 3: w^9
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dft4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);  // v[4c + d] = X[c + 4d]
+        const int64_t d0 = ((j - r) << 4) + r;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int d = 0; d < 4; ++d) out[d0 + (c + 4 * d) * Ns] = v[4 * c + d];
+    }
+}
+
 __global__ void __launch_bounds__(kPrThreads)
 pr_finalize_kernel(const float2* __restrict__ Z, int64_t n_fft, int64_t j0, int64_t N_f, float n,
                    float* __restrict__ P_out) {
@@ -160,24 +232,41 @@ cudaError_t launch_pr(const double* t, const double* X, int64_t N, const CurveSt
     int nl = 1;
     int L = 0;
     while ((int64_t(1) << L) < n_fft) ++L;
-    // first pass reads the FP64 grid
+    // radix 2 and/or 4 first for the remainder of log2 n_fft modulo 4, then
+    // radix 16; the first pass reads the FP64 grid
     float2* cur = z0;
     float2* nxt = z1;
-    int64_t Ns;
-    if (L & 1) {
+    int64_t Ns = 1;
+    const int rem = L & 3;
+    bool first = true;
+    auto flip = [&]() {
+        if (!first) {
+            float2* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        first = false;
+        ++nl;
+    };
+    if (rem == 1 || rem == 3) {
         fft_radix2_first<double2><<<blocks_for(n_fft / 2), kPrThreads, 0, st>>>(acc, cur, n_fft);
         Ns = 2;
-    } else {
-        fft_radix4_pass<double2><<<blocks_for(n_fft / 4), kPrThreads, 0, st>>>(acc, cur, n_fft, 1);
-        Ns = 4;
+        flip();
     }
-    ++nl;
-    for (; Ns < n_fft; Ns <<= 2) {
-        fft_radix4_pass<float2><<<blocks_for(n_fft / 4), kPrThreads, 0, st>>>(cur, nxt, n_fft, Ns);
-        float2* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        ++nl;
+    if (rem >= 2) {
+        if (first)
+            fft_radix4_pass<double2><<<blocks_for(n_fft / 4), kPrThreads, 0, st>>>(acc, cur, n_fft, Ns);
+        else
+            fft_radix4_pass<float2><<<blocks_for(n_fft / 4), kPrThreads, 0, st>>>(cur, nxt, n_fft, Ns);
+        Ns *= 4;
+        flip();
+    }
+    for (; Ns < n_fft; Ns <<= 4) {
+        if (first)
+            fft_radix16_pass<double2><<<blocks_for(n_fft / 16), kPrThreads, 0, st>>>(acc, cur, n_fft, Ns);
+        else
+            fft_radix16_pass<float2><<<blocks_for(n_fft / 16), kPrThreads, 0, st>>>(cur, nxt, n_fft, Ns);
+        flip();
     }
     pr_finalize_kernel<<<blocks_for(N_f), kPrThreads, 0, st>>>(cur, n_fft, j0, N_f, (float)N, P_out);
     ++nl;
