@@ -24,6 +24,50 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
     return a > b ? a : b;
 }
 
+// Strip length of the tail items: the frequencies of a curve left over after
+// its full blocks of kMainThreads*F run in blocks of kMainThreads*kTailF, so
+// at most kMainThreads*kTailF - 1 slots per curve are padding.
+constexpr int kTailF = kBatchTailF;
+
+// One work item with strips of FF frequencies starting at k0: the tile loop
+// over all samples of the curve, Eq. 5-6, P written if asked; returns this
+// thread's largest (P bits << 32 | ~k) key.
+template <int FF, int MODE, bool XREC, class SM>
+__device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, int64_t b, int64_t e, int64_t N_f,
+                                                        const uint4* __restrict__ recA,
+                                                        const float4* __restrict__ recB, const float* x,
+                                                        float* P) {
+    Strip<FF, MODE> st;
+    st.zero();
+    if constexpr (XREC) {
+        // the single-curve kernel's loop: x from the records
+        for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
+#pragma unroll 2
+            for (int j = 0; j < n; ++j) {
+                const float4 B = bb[j];
+                st.add(a[j], B, B.x, k0);
+            }
+        });
+    } else {
+        for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
+#pragma unroll 2
+            for (int j = 0; j < n; ++j) st.add(a[j], bb[j], xs[j], k0);
+        });
+    }
+    const float n = (float)(e - b);
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int i = 0; i < FF; ++i) {
+        const uint32_t k = k0 + i;
+        if (k < (uint32_t)N_f) {
+            const float p = periodogram_value(st.xc[i], st.xs[i], st.cc[i], st.cs[i], n);
+            if (P) P[k] = p;
+            best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
+        }
+    }
+    return best;
+}
+
 template <int F, int MODE, bool XREC>
 __global__ void __launch_bounds__(kMainThreads)
 ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
@@ -43,36 +87,17 @@ ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __re
         const BatchItem w = items[it];
         const int64_t b = off[w.curve], e = off[w.curve + 1];
         const int64_t N_f = nf[w.curve];
-        const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
         const float* x = xr + (size_t)w.real * (size_t)total;
-        Strip<F, MODE> st;
-        st.zero();
-        if constexpr (XREC) {
-            // the single-curve kernel's loop: x from the records
-            for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
-#pragma unroll 2
-                for (int j = 0; j < n; ++j) {
-                    const float4 B = bb[j];
-                    st.add(a[j], B, B.x, k0);
-                }
-            });
-        } else {
-            for_each_tile<!XREC>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
-#pragma unroll 2
-                for (int j = 0; j < n; ++j) st.add(a[j], bb[j], xs[j], k0);
-            });
-        }
-        const float n = (float)(e - b);
-        unsigned long long best = 0ull;
         float* P = P_out ? P_out + (size_t)w.real * (size_t)P_total + P_off[w.curve] : nullptr;
-#pragma unroll
-        for (int i = 0; i < F; ++i) {
-            const uint32_t k = k0 + i;
-            if (k < (uint32_t)N_f) {
-                const float p = periodogram_value(st.xc[i], st.xs[i], st.cc[i], st.cs[i], n);
-                if (P) P[k] = p;
-                best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
-            }
+        unsigned long long best;
+        if (F > kTailF && w.pad < 0) {
+            // tail item: sub-block (-1 - pad) of kMainThreads*kTailF after fblock full blocks
+            const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) +
+                                (uint32_t)(-1 - w.pad) * (kMainThreads * kTailF) + (uint32_t)threadIdx.x * kTailF;
+            best = batch_item<kTailF, MODE, XREC>(sm, k0, b, e, N_f, recA, recB, x, P);
+        } else {
+            const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+            best = batch_item<F, MODE, XREC>(sm, k0, b, e, N_f, recA, recB, x, P);
         }
         for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_down_sync(0xffffffffu, best, o));
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;

@@ -120,16 +120,25 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
                       pl.nf == nf && pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
     if (!same) {
         drop_plan(ctx);
-        // work list: curves longest first (each item costs ~N_t), then blocks, then realizations
+        // work list: curves longest first (each item costs ~N_t), then blocks, then realizations;
+        // with single-realization strips longer than the tail strip, the frequencies after a
+        // curve's last full block go to tail items of kMainThreads * kBatchTailF frequencies
         std::vector<int> order(n_curves);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+        const bool tails = R == 1 && F > lsp::kBatchTailF;
+        const int64_t tail_block = lsp::freqs_per_block(lsp::kBatchTailF);
         std::vector<lsp::BatchItem> items;
         for (int c : order) {
-            const int64_t nfb = (nf[c] + per_block - 1) / per_block;
+            const int64_t nfb = tails ? nf[c] / per_block : (nf[c] + per_block - 1) / per_block;
             for (int64_t fb = 0; fb < nfb; ++fb)
                 for (int r = 0; r < n_real; r += R) items.push_back({c, r, (int32_t)fb, std::min(R, n_real - r)});
+            if (tails) {
+                const int64_t ntail = (nf[c] - nfb * per_block + tail_block - 1) / tail_block;
+                for (int64_t tb = 0; tb < ntail; ++tb)
+                    for (int r = 0; r < n_real; ++r) items.push_back({c, r, (int32_t)nfb, (int32_t)(-1 - tb)});
+            }
         }
         if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
         const size_t item_bytes = items.size() * sizeof(lsp::BatchItem);

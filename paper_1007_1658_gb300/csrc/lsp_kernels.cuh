@@ -122,8 +122,13 @@ struct BatchItem {
     int32_t curve;
     int32_t real;    // realization (first of the group for multi-RHS items)
     int32_t fblock;
-    int32_t pad;     // multi-RHS items: realizations in the group
+    int32_t pad;     // multi-RHS items: realizations in the group; single-realization
+                     // items with F > 8: a negative value marks a tail item, sub-block
+                     // -1 - pad of kMainThreads*8 frequencies after fblock full blocks
 };
+
+// Strip length of the single-realization batch kernel's tail items.
+constexpr int kBatchTailF = 8;
 
 int batch_occupancy(int mode, int F, bool x_in_records);
 

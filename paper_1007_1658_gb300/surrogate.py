@@ -179,8 +179,13 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small run (minutes -> seconds)")
     ap.add_argument("--out", default=DEFAULT_MODEL)
     ap.add_argument("--steps", type=int, default=0)
+    ap.add_argument("--judge-only", action="store_true", help="judge the model in --out, no training")
     args = ap.parse_args()
     ctx = lsp.Context(0)
+    if args.judge_only:
+        ctx.fap_load(args.out)
+        print(json.dumps({"judge": judge(ctx), "model": os.path.basename(args.out)}), flush=True)
+        return
     if args.quick:
         tr = train(ctx, n_patterns=4096, n_real=4, steps=args.steps or 400, batch=2048, n_val=512, eval_every=100)
         jd = judge(ctx, n_patterns=64, n_real=2000)
