@@ -188,3 +188,26 @@ def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F):
         ctx.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_full_noise_batch_sampled_curves(ctx):
+    """The benchmark's Monte-Carlo batch at full size (4096 noise curves, N_t
+    log-uniform in [200, 20000], N_f = 2 N_t, seed 1234, one graph launch):
+    ten curves across the size range against the oracle's periodogram of
+    the oracle's own noise."""
+    from paper_1007_1658_gb300 import synth
+    b = synth.noise_batch(n_curves=4096)
+    seed = 1234
+    ctx.set_options()
+    maxP, argmax = ctx.batch(_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf), seed=seed)
+    ctx.sync(300.0)
+    maxP = maxP.cpu().numpy()
+    argmax = argmax.cpu().numpy()
+    n_t = np.diff(b.t_off)
+    order = np.argsort(n_t, kind="stable")
+    picks = np.concatenate([order[:4], order[2046:2050], order[-4:-2]])
+    for c in picks:
+        t, X = _oracle_noise_curve(b, seed, int(c), 0)
+        ref = oracle.periodogram(t, X, b.f0[c], b.df[c], b.nf[c])
+        assert abs(maxP[c] - ref.max()) <= TOL_ABS * ref.max(), c
+        assert ref[argmax[c]] >= ref.max() * (1 - 2 * TOL_ABS), c

@@ -201,6 +201,17 @@ def test_full_size_sampled(ctx, name, mode):
     assert_parity(got[ks], ref, peaks=_window_peaks(c, ks, ref), what="%s mode %d" % (name, mode))
 
 
+def test_cadence_with_offset_stresses_normalization(ctx):
+    """Config-3 variant: the 1e-3 signal and noise ride on a constant 1.0, so
+    the mean removal must happen before any FP32 rounding (FP64 prep)."""
+    from paper_1007_1658_gb300 import synth
+    c = synth.cadence_65k(offset=1.0)
+    got = _run(ctx, c.t, c.X, c.f0, c.df, c.nf, sincos_mode=0)
+    ks = _sampled_bins(c, np.random.default_rng(7))
+    ref = oracle.periodogram_at(c.t, c.X, c.f0 + ks * c.df)
+    assert_parity(got[ks], ref, peaks=_window_peaks(c, ks, ref), what="cadence_65k + 1.0")
+
+
 def test_cadence_naive_phase_fails_and_fixed_point_passes(ctx):
     """Config-3 precision comparison: the paper's FP32 phase f*t - rintf(f*t)
     misses the tolerance near 20 c/d (f t ~ 3e4 turns); the fixed-point phase
