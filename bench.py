@@ -228,6 +228,13 @@ def run_gpu(args, rank, world, dist):
     total_ms = shard.max_over_ranks(total_ms, dist, dev)
     value = world * terms * args.steps / (total_ms * 1e-3)
 
+    # latency of one small call (plain_1k: 1000 x 2000, device pointers)
+    small = synth.plain_1k()
+    ts_d, Xs_d = torch.from_numpy(small.t).to(dev), torch.from_numpy(small.X).to(dev)
+    Ps_d = torch.empty(small.nf, dtype=torch.float32, device=dev)
+    lat_fn = lambda: ctx.periodogram(ts_d, Xs_d, small.f0, small.df, small.nf, out=Ps_d)
+    lat_ms = _time_calls(torch, stream, lat_fn, 5, 20, flush)
+
     # end to end through the C ABI with pinned host buffers (copies inside)
     e2e_val = None
     if args.e2e:
@@ -270,6 +277,8 @@ def run_gpu(args, rank, world, dist):
             "value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(c.t.nbytes + c.X.nbytes),
             "d2h_bytes_per_step": int(c.nf * 4)},
         "gpu_launches": int(launches),
+        "latency": {"workload": "plain_1k: 1000 x 2000", "us_per_call": lat_ms * 1e3,
+                    "note": "prep + main (+ finalize), device pointers, median of 20"},
         "clocks": clk.summary(),
     }
     if args.cpu_baseline and world == 1:
@@ -277,6 +286,8 @@ def run_gpu(args, rank, world, dist):
     if args.batch:
         line["batched_mc"] = run_batch_bench(ctx, torch, dev, stream, args)
         line["batched_mc"]["multi_rhs"] = run_mrhs_bench(torch, dev, stream)
+        if args.cpu_baseline and world == 1:
+            line["batched_mc"]["cpu_baseline"] = batch_cpu_sample()
     if args.gls:
         line["floating_mean"] = run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms)
     if args.paper:
@@ -428,6 +439,25 @@ def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
                              roof[0], roof[1], sms, peaks["sm_max_mhz"], peak_src),
                          "main_ms": float(np.mean(main_ms))},
             "clocks": clk.summary()}
+
+
+def batch_cpu_sample(n_sample=32, seed=1234):
+    """The oracle on a random subset of the Monte-Carlo batch's curves (same
+    patterns, same Philox noise), as curves/s and terms/s on the host cores."""
+    import oracle
+    from paper_1007_1658_gb300 import synth
+    b = synth.noise_batch(n_curves=4096)
+    picks = np.random.default_rng(5).choice(b.n, n_sample, replace=False)
+    terms = 0
+    t0 = time.perf_counter()
+    for c in picks:
+        t = b.curve_t(int(c))
+        X = oracle.noise(seed, int(c), 0, t.size)
+        oracle.periodogram(t, X, b.f0[c], b.df[c], b.nf[c])
+        terms += t.size * int(b.nf[c])
+    sec = time.perf_counter() - t0
+    return {"value": n_sample / sec, "unit": "curves/s", "terms_per_s": terms / sec, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": "%d random curves of the 4096 (%.3g terms)" % (n_sample, terms)}
 
 
 def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64):

@@ -37,9 +37,32 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
 
 }  // namespace
 
+// Kernel mode and strip length for the options, before any size-dependent
+// choice: the strip lengths measured best on GB300 for each mode on large
+// curves (gapped_100k), or the one asked for.
+void lsp::host::default_mode_F(const lsp_options& o, int* mode, int* F) {
+    if (o.phase_mode == LSP_PHASE_NAIVE_FP32) {
+        *mode = lsp::kModeNaive;
+        *F = 8;
+    } else if (o.sincos_mode == LSP_SINCOS_MUFU) {
+        *mode = lsp::kModeMufu;
+        *F = 8;
+    } else if (o.sincos_mode == LSP_SINCOS_RECUR) {
+        *mode = lsp::kModeRecur;
+        *F = 16;
+    } else if (o.sincos_mode == LSP_SINCOS_RECUR3_X2) {
+        *mode = lsp::kModeRecur3x2;
+        *F = 24;
+    } else {
+        *mode = lsp::kModeRecur3;
+        *F = 24;
+    }
+    if (o.freqs_per_thread) *F = o.freqs_per_thread;
+}
+
 // Launch shape: mode, strip length F, N_t split.  The split is chosen so the
 // grid fills whole waves of resident CTAs while every chunk keeps at least
-// one tile of samples.
+// one tile of samples; small problems also get shorter strips.
 MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
     lsp_options o = ctx->opt;
@@ -52,24 +75,21 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
             o.split = (int)std::min<int64_t>(te->split, std::max<int64_t>(1, N / lsp::kTile));
         }
     }
-    // Strip lengths measured best on GB300 for each mode (gapped_100k workload).
-    if (o.phase_mode == LSP_PHASE_NAIVE_FP32) {
-        s.mode = lsp::kModeNaive;
-        s.F = 8;
-    } else if (o.sincos_mode == LSP_SINCOS_MUFU) {
-        s.mode = lsp::kModeMufu;
-        s.F = 8;
-    } else if (o.sincos_mode == LSP_SINCOS_RECUR) {
-        s.mode = lsp::kModeRecur;
-        s.F = 16;
-    } else if (o.sincos_mode == LSP_SINCOS_RECUR3_X2) {
-        s.mode = lsp::kModeRecur3x2;
-        s.F = 24;
-    } else {
-        s.mode = lsp::kModeRecur3;
-        s.F = 24;
+    default_mode_F(o, &s.mode, &s.F);
+    if (o.freqs_per_thread) {
+        s.F = o.freqs_per_thread;
+    } else if (s.mode != lsp::kModeNaive) {
+        // small problems: shorter strips until the grid (at one tile of samples
+        // per chunk) fills a wave of resident CTAs, down to 4 frequencies
+        const int64_t max_split = std::max<int64_t>(1, N / lsp::kTile);
+        for (int f : {24, 16, 8, 4}) {
+            if (f > s.F) continue;
+            s.F = f;
+            const int64_t per = lsp::freqs_per_block(f);
+            const int64_t slots = (int64_t)std::max(1, lsp::main_occupancy(s.mode, f)) * std::max(1, ctx->sms);
+            if ((N_f + per - 1) / per * max_split >= slots) break;
+        }
     }
-    if (o.freqs_per_thread) s.F = o.freqs_per_thread;
     finish_shape(ctx, s, lsp::main_occupancy(s.mode, s.F), N, N_f, o.split);
     return s;
 }

@@ -67,17 +67,17 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
     const bool noise = X == nullptr;
 
     // ---- launch shape: the single-curve choice of mode and strip length ----
-    const MainShape shape = choose_shape(ctx, 2 * lsp::kTile, 1);
-    if (shape.mode == lsp::kModeNaive)
+    int mode = 0, F1 = 0;
+    default_mode_F(ctx->opt, &mode, &F1);
+    if (mode == lsp::kModeNaive)
         return fail(ctx, LSP_ERR_UNSUPPORTED, "lsp_batch does not offer the naive FP32 phase");
-    const int mode = shape.mode;
     // realizations per pass over the samples (multi-RHS) and the strip length that goes with it
     int R = 1;
     if (n_real > 1) {
         R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : 4;
         if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
     }
-    const int F = R == 1 ? shape.F : (R == 8 ? 4 : 8);
+    const int F = R == 1 ? F1 : (R == 8 ? 4 : 8);
     const int64_t per_block = lsp::freqs_per_block(F);
 
     // ---- device views of the inputs (host arrays are copied in, outside the graph) ----

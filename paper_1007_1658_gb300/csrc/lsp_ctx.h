@@ -208,6 +208,9 @@ inline lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf,
     return LSP_OK;
 }
 
+// Kernel mode and strip length for the options, with no size-dependent choice.
+void default_mode_F(const lsp_options& o, int* mode, int* F);
+
 // Launch shape of the single-curve path for the context's options.
 lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
 

@@ -104,7 +104,8 @@ extern "C" lsp_status lsp_autotune(lsp_ctx* ctx, int64_t N_t, int64_t N_f, lsp_o
     for (float v : ref) pmax = std::max(pmax, v);
     struct Cand { int sincos, F; };
     const Cand cands[] = {{LSP_SINCOS_RECUR3, 24}, {LSP_SINCOS_RECUR3, 16}, {LSP_SINCOS_RECUR3, 8},
-                          {LSP_SINCOS_RECUR, 16},  {LSP_SINCOS_RECUR, 8},   {LSP_SINCOS_MUFU, 8}};
+                          {LSP_SINCOS_RECUR3, 4},  {LSP_SINCOS_RECUR, 16},  {LSP_SINCOS_RECUR, 8},
+                          {LSP_SINCOS_MUFU, 8}};
     TuneEntry best{bucket(N_t), bucket(N_f), 0, 0, 0, 1e30f};
     for (const Cand& c : cands) {
         // the heuristic split of this candidate, then half and double of it
@@ -113,7 +114,8 @@ extern "C" lsp_status lsp_autotune(lsp_ctx* ctx, int64_t N_t, int64_t N_f, lsp_o
         ctx->opt.freqs_per_thread = c.F;
         ctx->opt.split = 0;
         const int base_split = choose_shape(ctx, N_t, N_f).split;
-        const int splits[3] = {base_split, std::max(1, base_split / 2), std::min<int>(base_split * 2, (int)std::max<int64_t>(1, N_t / lsp::kTile))};
+        const int max_split = (int)std::max<int64_t>(base_split, std::max<int64_t>(1, N_t / lsp::kTile));
+        const int splits[3] = {base_split, std::max(1, base_split / 2), std::min<int>(base_split * 2, max_split)};
         for (int si = 0; si < 3; ++si) {
             if (si > 0 && splits[si] == base_split) continue;
             if ((rs = run(c.sincos, c.F, splits[si], &got, &ms)) != LSP_OK) {
