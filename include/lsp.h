@@ -132,7 +132,9 @@ lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64
  * centred cos and sin are linearly dependent on the samples (f = 0, Nyquist
  * of an even grid) the fit uses the remaining direction; where both vanish,
  * P = 0.  Same t, X, grid and pointer rules as lsp_periodogram; dy[N_t]
- * (FP64, optional, host or device) must be finite and > 0.  N_t >= 3.
+ * (FP64, optional, host or device) must be finite and > 0, with 1/dy^2 a
+ * finite nonzero FP32 number (about 1e-19 < dy < 1e19: the weights are formed
+ * in FP32, summed in FP64).  N_t >= 3.
  * sincos_mode selects MUFU, RECUR, RECUR3 or RECUR3_X2 (AUTO: RECUR3_X2);
  * strips are 8 or 16 frequencies (freqs_per_thread 8 or 16; other values use
  * 16, 8 for MUFU).

@@ -51,6 +51,18 @@ __device__ double block_min(double v, double* sh) {
     return sh[32];
 }
 
+// Joins the statistics (weight sum n, mean, M2 = sum w (x - mean)^2) of a
+// second group into the first: one division (Chan, Golub & LeVeque 1979).
+__device__ __forceinline__ void chan_merge(double& n, double& mean, double& m2, double nb, double mb, double m2b) {
+    if (!(nb > 0.0)) return;
+    const double nn = n + nb;
+    const double r = nb / nn;
+    const double d = mb - mean;
+    mean += d * r;
+    m2 += m2b + d * d * n * r;
+    n = nn;
+}
+
 // Statistics of one curve, or of one slice of it (G CTAs per curve): t_ref =
 // min t, mean and population variance of X (two passes over the slice, FP64),
 // non-finite detection.  With G > 1 each CTA leaves (n, mean, M2, min t) of
@@ -78,12 +90,15 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
     const int64_t se = min(e, sb + L);
     double s = 0.0, tmin = DBL_MAX, ws = 0.0;
     int bad = 0, badw = 0;
+#pragma unroll 4
     for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
         const double x = X ? X[j] : 0.0, tj = t[j];
         bad |= !(isfinite(x) && isfinite(tj));
         if (dy) {
+            // weights in FP32 (relative error ~1e-7; FP64 division is slow on this part)
             const double ej = dy[j];
-            const double wj = 1.0 / (ej * ej);
+            const float ef = (float)ej;
+            const double wj = (double)(1.f / (ef * ef));
             badw |= !(isfinite(ej) && ej > 0.0 && isfinite(wj) && wj > 0.0);
             ws += wj;
             s += wj * x;
@@ -100,11 +115,12 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
     const double mean_g = cnt > 0 ? s / cnt : 0.0;
     double v = 0.0;
     if (X) {
+#pragma unroll 4
         for (int64_t j = sb + threadIdx.x; j < se; j += blockDim.x) {
             const double d = X[j] - mean_g;
             if (dy) {
-                const double ej = dy[j];
-                v = fma(d / (ej * ej), d, v);
+                const float ef = (float)dy[j];
+                v = fma(d * (double)(1.f / (ef * ef)), d, v);
             } else {
                 v = fma(d, d, v);
             }
@@ -126,27 +142,37 @@ prep_stats_kernel(const double* __restrict__ t, const double* __restrict__ X,
         }
         __syncthreads();
         if (!last) return;
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // warp 0 merges the G <= kMaxStatSlices slices: lane l takes slices
+            // l, l + 32, ... in order, then a fixed shuffle tree joins the lanes
+            // (Chan, Golub & LeVeque's update), so the order never depends on
+            // which CTA finished last
             __threadfence();
+            const int lane = threadIdx.x;
             tot_n = 0.0;
             mean = 0.0;
             m2 = 0.0;
             tmin = DBL_MAX;
             bad = 0;
             const StatPart* pp = parts + (size_t)c * G;
-            for (int q = 0; q < G; ++q) {
-                const double nb = __ldcg(&pp[q].n);
-                if (nb <= 0.0) continue;
-                const double mb = __ldcg(&pp[q].mean), m2b = __ldcg(&pp[q].m2);
-                const double nn = tot_n + nb;
-                const double d = mb - mean;
-                mean += d * (nb / nn);
-                m2 += m2b + d * d * (tot_n * nb / nn);
-                tot_n = nn;
+            for (int q = lane; q < G; q += 32) {
+                chan_merge(tot_n, mean, m2, __ldcg(&pp[q].n), __ldcg(&pp[q].mean), __ldcg(&pp[q].m2));
                 tmin = fmin(tmin, __ldcg(&pp[q].tmin));
                 bad |= __ldcg(&pp[q].bad);
             }
-            counters[c] = 0u;  // ready for the next call
+            for (int o = 1; o < 32; o <<= 1) {
+                const double nb = __shfl_down_sync(0xffffffffu, tot_n, o);
+                const double mb = __shfl_down_sync(0xffffffffu, mean, o);
+                const double m2b = __shfl_down_sync(0xffffffffu, m2, o);
+                const double tb = __shfl_down_sync(0xffffffffu, tmin, o);
+                const int bb = __shfl_down_sync(0xffffffffu, bad, o);
+                if ((lane & (2 * o - 1)) == 0 && lane + o < 32) {
+                    chan_merge(tot_n, mean, m2, nb, mb, m2b);
+                    tmin = fmin(tmin, tb);
+                    bad |= bb;
+                }
+            }
+            if (lane == 0) counters[c] = 0u;  // ready for the next call
         }
     }
     if (threadIdx.x == 0) {
@@ -178,6 +204,24 @@ __device__ __forceinline__ uint64_t frac_turns64(double a, double b) {
     return U + (uint64_t)E;
 }
 
+// cos/sin(2 pi u) of a 64-bit fixed-point turn u (read as signed, so the turn
+// is in [-1/2, 1/2)): the top 24 bits go to sincospif as an exact FP32
+// argument; the remaining bits (at most 2^-24 turn, an angle d < 3.8e-7 rad)
+// enter by the angle-addition formula to first order, cos(a + d) = cos a -
+// d sin a, sin(a + d) = sin a + d cos a, whose neglected terms are below
+// d^2/2 < 2^-43.  FP32 throughout (FP64 transcendentals are slow here).
+__device__ __forceinline__ void rotation_of(uint64_t u, float* c, float* s) {
+    const int64_t su = (int64_t)u;
+    const int64_t top = su >> 40;  // in [-2^23, 2^23): exact as a float
+    const float th = (float)top * 0x1p-24f;
+    const float tl = (float)(su - top * (int64_t(1) << 40)) * 0x1p-64f;
+    float sh, ch;
+    sincospif(2.f * th, &sh, &ch);
+    const float d = 6.28318530717958647692f * tl;
+    *c = fmaf(-d, sh, ch);
+    *s = fmaf(d, ch, sh);
+}
+
 __global__ void __launch_bounds__(256)
 prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
                     const int64_t* __restrict__ off, int64_t n0,
@@ -192,27 +236,28 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
     const double f0 = f0a ? f0a[c] : f0s;
     const double df = dfa ? dfa[c] : dfs;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // 1/sqrt(sum of weights): the weight sum from the stats, or N without errors
+    const float isw = qout ? (float)rsqrt(dy ? st.pad : (double)(e - b)) : 0.f;
     for (int64_t j = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < e; j += stride) {
         const double tt = t[j] - st.t_ref;
         const uint64_t u = frac_turns64(tt, df);
         const uint64_t v = frac_turns64(tt, f0) + kPhaseOffset;
         const uint32_t du = (uint32_t)((u + (1ull << 31)) >> 32);
         // rotation of one grid step, cos/sin(2 pi u), from the exact fixed-point turn
-        const double turn = (double)(int64_t)u * 0x1p-64;
-        double sn, cs;
-        sincospi(2.0 * turn, &sn, &cs);
+        float sn, cs;
+        rotation_of(u, &cs, &sn);
         float xh;
         if (qout) {
             // floating-mean form: q = sqrt(w_j) with w_j = v_j / sum v (sum w = 1;
             // equal weights without dy), x = q (X - mean_w) / sd_w, so sum x^2 = 1
-            const double q = dy ? rsqrt(st.pad) / dy[j] : rsqrt((double)(e - b));
-            qout[j] = (float)q;
-            xh = (float)((X[j] - st.mean) * st.inv_sd * q);
+            const float q = dy ? isw / (float)dy[j] : isw;
+            qout[j] = q;
+            xh = (float)((X[j] - st.mean) * st.inv_sd) * q;
         } else {
             xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
         }
         recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
-        recB[j] = make_float4(xh, (float)cs, (float)sn, __uint_as_float(du));
+        recB[j] = make_float4(xh, cs, sn, __uint_as_float(du));
         if (recN) recN[j] = make_float2(xh, __double2float_rn(tt));
         if (xout) xout[j] = xh;
     }
@@ -222,7 +267,7 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
 
 int prep_stats_slices(int n_curves, int64_t n0) {
     if (n_curves > 1) return 1;
-    int64_t g = n0 / 8192;
+    int64_t g = n0 / 2048;
     return (int)(g < 1 ? 1 : (g > kMaxStatSlices ? kMaxStatSlices : g));
 }
 
