@@ -155,8 +155,9 @@ __device__ __forceinline__ float gls_value(double XC, double XS, double C, doubl
     const double R = sqrt(A * A + B * B);
     double c2 = 1.0, s2 = 0.0;
     if (R > 0.0) {
-        c2 = A / R;
-        s2 = B / R;
+        const double iR = 1.0 / R;
+        c2 = A * iR;
+        s2 = B * iR;
     }
     const double z2 = XC * XC + XS * XS;
     const double cross = c2 * (XC * XC - XS * XS) + s2 * (2.0 * XC * XS);
@@ -211,19 +212,28 @@ gls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB,
     row(5, st.cs);
 }
 
-// Per-chunk partial sums added in chunk order in FP64 (deterministic), then p.
+// Per-chunk partial sums added in chunk order with compensated (Neumaier)
+// FP32 sums (deterministic; FP64 adds are slow on this part), then p in FP64.
 __global__ void __launch_bounds__(256)
 gls_finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, int N_f, double n,
                     float* __restrict__ P_out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N_f) return;
-    double s[kGlsSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    float s[kGlsSums], c[kGlsSums];
+#pragma unroll
+    for (int r = 0; r < kGlsSums; ++r) s[r] = c[r] = 0.f;
     for (int sp = 0; sp < split; ++sp) {
         const float* p = part + (size_t)sp * kGlsSums * (size_t)nf_pad + k;
 #pragma unroll
-        for (int r = 0; r < kGlsSums; ++r) s[r] += (double)p[(size_t)r * nf_pad];
+        for (int r = 0; r < kGlsSums; ++r) {
+            const float v = p[(size_t)r * nf_pad];
+            const float t = s[r] + v;
+            c[r] += fabsf(s[r]) >= fabsf(v) ? (s[r] - t) + v : (v - t) + s[r];
+            s[r] = t;
+        }
     }
-    P_out[k] = gls_value(s[0], s[1], s[2], s[3], s[4], s[5], n);
+    P_out[k] = gls_value((double)s[0] + c[0], (double)s[1] + c[1], (double)s[2] + c[2], (double)s[3] + c[3],
+                         (double)s[4] + c[4], (double)s[5] + c[5], n);
 }
 
 using GlsFn = void (*)(const uint4*, const float4*, const float*, int64_t, int64_t, int, int64_t, float*, float*);

@@ -62,7 +62,9 @@ void lsp::host::default_mode_F(const lsp_options& o, int* mode, int* F) {
 
 // Launch shape: mode, strip length F, N_t split.  The split is chosen so the
 // grid fills whole waves of resident CTAs while every chunk keeps at least
-// one tile of samples; small problems also get shorter strips.
+// one tile of samples (chunks below a tile measured slower: the extra
+// partial sums cost more than the parallelism gains); small problems get
+// shorter strips instead.
 MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
     lsp_options o = ctx->opt;
