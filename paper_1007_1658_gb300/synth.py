@@ -219,4 +219,5 @@ WORKLOADS = {
     "plain_1k": plain_1k,
     "gapped_100k": gapped_100k,
     "cadence_65k": cadence_65k,
+    "corot_382k": corot_382k,
 }

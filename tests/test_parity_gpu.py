@@ -2,10 +2,11 @@
 
 Tolerance (written here, from the required bound): |dP| <= 1e-4 max P and
 relative error <= 1e-4 at the ten largest peaks.  Small cases are compared on
-the whole grid; the full-size workloads (100k x 200k and 65,536 x 318,500, in
-the launch configuration the benchmark times) are compared on sampled bins
-that the oracle evaluates one by one: random bins across the grid plus windows
-around every injected frequency, where the peaks are.
+the whole grid; the full-size workloads (100k x 200k, 65,536 x 318,500 and the
+paper shape 382,003 x 1,528,064, in the launch configuration the benchmark
+times) are compared on sampled bins that the oracle evaluates one by one:
+random bins across the grid plus windows around every injected frequency,
+where the peaks are.
 """
 import numpy as np
 import pytest
@@ -188,7 +189,8 @@ def _window_peaks(c, ks, ref):
 
 
 @pytest.mark.parametrize("name,mode", [("gapped_100k", 2), ("gapped_100k", 1), ("gapped_100k", 3),
-                                       ("cadence_65k", 2), ("cadence_65k", 1), ("cadence_65k", 3)])
+                                       ("cadence_65k", 2), ("cadence_65k", 1), ("cadence_65k", 3),
+                                       ("corot_382k", 0)])
 def test_full_size_sampled(ctx, name, mode):
     from paper_1007_1658_gb300 import synth
     c = synth.WORKLOADS[name]()
