@@ -18,7 +18,7 @@
 // A thread forms the top 32 bits once per sample for its first k, so the
 // phase never loses accuracy however large f t grows.
 //
-// sin/cos, three modes (ls_device.cuh, Strip::add):
+// sin/cos modes (ls_device.cuh, Strip::add and Strip<F, kRecur3x2>):
 //   MUFU   -- every (j, k) takes the hardware sin/cos of the phase (the
 //             paper's __sincosf, Sec. 4.3), stepping the 32-bit phase by
 //             round(u / 2^32): 2 SFU ops per term.
