@@ -382,6 +382,10 @@ int oracle_window_at(const double *t, int64_t n, const double *freqs, int64_t nf
  * Philox-4x32-10 (Salmon, Moraes, Dror & Shaw 2011, "Parallel random
  * numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies and
  * a Feistel-like swap, with a Weyl-sequence key schedule between rounds.
+ * Parity unpinned against the published known-answer vectors (not reproduced
+ * here): only statistical pins hold it, and the GPU generator is compared
+ * with this one.  What the Monte-Carlo results depend on -- independent
+ * N(0,1) draws -- is pinned downstream by exact Beta and Dirichlet laws.
  */
 void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
 {
