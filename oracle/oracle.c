@@ -138,7 +138,7 @@ static double direct_one(const double *tt, const double *x, int64_t n, double f)
     return 0.5 * P;
 }
 
-/* Shared driver: normalize, shift times, evaluate one routine per frequency. */
+/* Shared loop: normalize, shift times, evaluate one routine per frequency. */
 typedef double (*one_freq_fn)(const double *tt, const double *x, int64_t n, double f);
 
 static int run_at(one_freq_fn fn, const double *t, const double *X, int64_t n,

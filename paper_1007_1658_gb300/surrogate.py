@@ -5,11 +5,11 @@ features and the network's forward, backward and Adam steps all run in
 liblsp.so's kernels (lsp_batch, lsp_fap_*); this module draws sampling
 patterns (synth.noise_batch), hands arrays to the C ABI and loops.
 
-  python -m paper_1007_1658_gb300.surrogate [--quick] [--out model.lspfap]
+  python -m paper_1007_1658_gb300.surrogate [--quick] [--out model.lspfap] [--evaluate-only]
 
-trains on noise periodograms the batched engine generates and judges the
+trains on noise periodograms the batched engine generates and evaluates the
 trained network against brute-force Monte Carlo on held-out patterns,
-printing one JSON report.
+printing one JSON report (--evaluate-only: evaluate the model in --out).
 """
 from __future__ import annotations
 
@@ -132,7 +132,7 @@ def eq3_quantiles(n_t, n_f):
     return 0.5 * n_t * (-np.expm1(2.0 / (n_t - 3.0) * np.log(a)))
 
 
-def judge(ctx: lsp.Context, n_patterns=256, n_real=10000, seed=777001):
+def evaluate(ctx: lsp.Context, n_patterns=256, n_real=10000, seed=777001):
     """Held-out patterns: surrogate quantiles and Eq. 3's against brute-force
     Monte Carlo with n_real noise realizations each; GPU seconds of both."""
     import torch
@@ -179,21 +179,22 @@ def main():
     ap.add_argument("--quick", action="store_true", help="small run (minutes -> seconds)")
     ap.add_argument("--out", default=DEFAULT_MODEL)
     ap.add_argument("--steps", type=int, default=0)
-    ap.add_argument("--judge-only", action="store_true", help="judge the model in --out, no training")
+    ap.add_argument("--evaluate-only", action="store_true",
+                    help="evaluate the model in --out against Monte Carlo, no training")
     args = ap.parse_args()
     ctx = lsp.Context(0)
-    if args.judge_only:
+    if args.evaluate_only:
         ctx.fap_load(args.out)
-        print(json.dumps({"judge": judge(ctx), "model": os.path.basename(args.out)}), flush=True)
+        print(json.dumps({"evaluation": evaluate(ctx), "model": os.path.basename(args.out)}), flush=True)
         return
     if args.quick:
         tr = train(ctx, n_patterns=4096, n_real=4, steps=args.steps or 400, batch=2048, n_val=512, eval_every=100)
-        jd = judge(ctx, n_patterns=64, n_real=2000)
+        jd = evaluate(ctx, n_patterns=64, n_real=2000)
     else:
         tr = train(ctx, steps=args.steps or 2000)
-        jd = judge(ctx)
+        jd = evaluate(ctx)
     ctx.fap_save(args.out)
-    print(json.dumps({"train": tr, "judge": jd, "model": os.path.basename(args.out)}), flush=True)
+    print(json.dumps({"train": tr, "evaluation": jd, "model": os.path.basename(args.out)}), flush=True)
 
 
 if __name__ == "__main__":

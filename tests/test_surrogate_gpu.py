@@ -189,7 +189,7 @@ def test_committed_model_beats_eq3_against_monte_carlo(lsp):
     from paper_1007_1658_gb300 import surrogate as SU
     ctx = lsp.Context(0)
     ctx.fap_load(SU.DEFAULT_MODEL)
-    jd = SU.judge(ctx, n_patterns=48, n_real=3000, seed=424242)
+    jd = SU.evaluate(ctx, n_patterns=48, n_real=3000, seed=424242)
     sur = np.array(jd["mean_rel_err_surrogate"])
     eq3 = np.array(jd["mean_rel_err_eq3"])
     assert sur.max() <= 0.05, sur
