@@ -74,8 +74,10 @@ typedef enum lsp_phase_mode {
 typedef struct lsp_options {
     int32_t sincos_mode;      /* lsp_sincos_mode                                       */
     int32_t phase_mode;       /* lsp_phase_mode                                        */
-    int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|16|24,
-                                 or 20|28 with the recurrences                          */
+    int32_t freqs_per_thread; /* adjacent frequencies per thread: 0 = auto, else 4|8|12|16|24,
+                                 or 20|28 with the recurrences; multi-realization
+                                 batches take it when their kernels have that shape
+                                 (12 with 4 realizations, 16 with 2)                    */
     int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */

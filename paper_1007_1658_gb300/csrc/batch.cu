@@ -193,6 +193,7 @@ BatchFn batch_fn_f(int F) {
     switch (F) {
         case 4: return ls_batch_kernel<4, MODE, XREC>;
         case 8: return ls_batch_kernel<8, MODE, XREC>;
+        case 12: return ls_batch_kernel<12, MODE, XREC>;
         case 16: return ls_batch_kernel<16, MODE, XREC>;
         case 20: return MODE == kMufu ? nullptr : ls_batch_kernel<20, MODE, XREC>;
         case 24: return ls_batch_kernel<24, MODE, XREC>;
@@ -220,7 +221,9 @@ using MrhsFn = BatchFn;
 template <int MODE>
 MrhsFn mrhs_fn_f(int F, int R) {
     if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, MODE>;
+    if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, MODE>;
     if (F == 8 && R == 2) return ls_mrhs_kernel<8, 2, MODE>;
+    if (F == 16 && R == 2) return ls_mrhs_kernel<16, 2, MODE>;
     if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, MODE>;
     return nullptr;
 }

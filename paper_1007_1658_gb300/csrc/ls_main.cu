@@ -172,6 +172,7 @@ MainFn main_fn_f(int F) {
     switch (F) {
         case 4: return ls_main_kernel<4, MODE>;
         case 8: return ls_main_kernel<8, MODE>;
+        case 12: return ls_main_kernel<12, MODE>;
         case 16: return ls_main_kernel<16, MODE>;
         case 20: return MODE == kMufu ? nullptr : ls_main_kernel<20, MODE>;
         case 24: return ls_main_kernel<24, MODE>;
@@ -194,6 +195,7 @@ NaiveFn naive_fn(int F) {
     switch (F) {
         case 4: return ls_naive_kernel<4>;
         case 8: return ls_naive_kernel<8>;
+        case 12: return ls_naive_kernel<12>;
         case 16: return ls_naive_kernel<16>;
         case 24: return ls_naive_kernel<24>;
         default: return nullptr;

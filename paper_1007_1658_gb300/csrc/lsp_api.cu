@@ -23,8 +23,8 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
     if (o->phase_mode < 0 || o->phase_mode > 1)
         return fail(ctx, LSP_ERR_INVALID_ARG, "phase_mode %d out of range", o->phase_mode);
     const int F = o->freqs_per_thread;
-    if (F != 0 && F != 4 && F != 8 && F != 16 && F != 20 && F != 24 && F != 28)
-        return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8, 16, 20, 24 or 28");
+    if (F != 0 && F != 4 && F != 8 && F != 12 && F != 16 && F != 20 && F != 24 && F != 28)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8, 12, 16, 20, 24 or 28");
     if ((F == 20 || F == 28) && (o->sincos_mode == LSP_SINCOS_MUFU || o->phase_mode == LSP_PHASE_NAIVE_FP32))
         return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread 20 and 28 are recurrence-only");
     if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");

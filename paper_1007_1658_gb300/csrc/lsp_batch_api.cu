@@ -77,7 +77,11 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : 4;
         if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
     }
-    const int F = R == 1 ? F1 : (R == 8 ? 4 : 8);
+    // strip lengths measured best on GB300 for each group size (256 patterns x 64 realizations)
+    int F = R == 1 ? F1 : (R == 8 ? 4 : (R == 4 ? 12 : 16));
+    // multi-realization strips: a strip length asked for replaces the default when that shape exists
+    if (R > 1 && ctx->opt.freqs_per_thread && lsp::mrhs_occupancy(mode, ctx->opt.freqs_per_thread, R) > 0)
+        F = ctx->opt.freqs_per_thread;
     const int64_t per_block = lsp::freqs_per_block(F);
 
     // ---- device views of the inputs (host arrays are copied in, outside the graph) ----

@@ -142,7 +142,7 @@ cudaError_t launch_batch(int mode, int F, bool x_in_records, int grid, const Bat
 
 // Multi-RHS batch: items carry a group of up to R realizations (real = first,
 // pad = count) sharing phases, recurrence and CC/CS; shapes (F, R) in
-// {(8, 4), (8, 2), (4, 8)}.
+// {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)}.
 int mrhs_occupancy(int mode, int F, int R);
 cudaError_t launch_mrhs(int mode, int F, int R, int grid, const BatchItem* items, int n_items, unsigned* head,
                         const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,

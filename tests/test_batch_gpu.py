@@ -167,7 +167,7 @@ def test_noise_periodograms_follow_the_beta_law(ctx):
     assert stats.kstest(z, stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
 
 
-@pytest.mark.parametrize("R,F", [(2, 8), (4, 8), (8, 4)])
+@pytest.mark.parametrize("R,F", [(2, 8), (2, 16), (4, 8), (4, 12), (8, 4)])
 def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F):
     """Groups of R realizations share the phase, the recurrence and CC/CS; each
     (frequency, realization) must come out bit for bit as the one-at-a-time

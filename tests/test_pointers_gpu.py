@@ -30,7 +30,8 @@ def test_mixed_pointer_sides_agree(lsp):
     c = synth.with_errors(synth.plain_1k)
     with lsp.Context(0) as ctx:
         ref = ctx.periodogram(c.t, c.X, c.f0, c.df, c.nf)
-        a = ctx.periodogram(_dev(c.t), c.X, c.f0, c.df, c.nf)               # t device, X host, P host
+        a = np.empty(c.nf, np.float32)
+        ctx.periodogram(_dev(c.t), c.X, c.f0, c.df, c.nf, out=a)            # t device, X host, P host
         out = torch.empty(c.nf, dtype=torch.float32, device="cuda")
         ctx.periodogram(c.t, _dev(c.X), c.f0, c.df, c.nf, out=out)          # t host, X device, P device
         ctx.sync(30.0)
@@ -40,7 +41,8 @@ def test_mixed_pointer_sides_agree(lsp):
         ctx.sync(30.0)
         assert np.array_equal(g_ref, g.cpu().numpy())
         p_ref = ctx.press_rybicki(c.t, c.X, c.f0, c.df, c.nf)
-        p = ctx.press_rybicki(_dev(c.t), c.X, c.f0, c.df, c.nf)
+        p = np.empty(c.nf, np.float32)
+        ctx.press_rybicki(_dev(c.t), c.X, c.f0, c.df, c.nf, out=p)
         assert np.max(np.abs(p_ref - p)) <= 1e-6 * p_ref.max()
 
 
