@@ -147,6 +147,23 @@ lsp_status lsp_periodogram_gls(lsp_ctx *ctx, const double *t, const double *X, c
                                int64_t N_t, double f_0, double df, int64_t N_f, float *P_out);
 
 /*
+ * The floating-mean periodogram of many measured curves in one persistent
+ * launch (the lsp_batch layout without noise realizations): curve c has
+ * samples t[t_off[c] .. t_off[c+1]) with values X and optional errors dy in the
+ * same layout (NULL: equal weights), at least 3 samples, and its own grid
+ * f_0[c] + k df[c], k < N_f[c].  Outputs as in lsp_batch with n_real = 1: P
+ * of curve c at P_out[P_off[c] + k] (optional), per-curve max P and its bin
+ * (optional; argmax -1 for an empty grid).  Pointers host or device; any host
+ * output makes the call blocking.  The call shares lsp_batch's workspace, so
+ * a later lsp_batch on the same context re-plans its graph.
+ * Errors: as lsp_periodogram_gls, plus INVALID_ARG for bad metadata.
+ */
+lsp_status lsp_batch_gls(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, const double *t,
+                         const double *X, const double *dy, const double *f_0, const double *df,
+                         const int64_t *N_f, float *P_out, const int64_t *P_off, float *maxP_out,
+                         int32_t *argmax_out);
+
+/*
  * Fast approximate P_n by the method of Press & Rybicki (1989), which the
  * paper's introduction cites as the O(N log N) alternative to the direct
  * evaluation: the normalized data are spread ("extirpolated") onto a uniform

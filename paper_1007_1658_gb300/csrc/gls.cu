@@ -236,6 +236,90 @@ gls_finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, i
                          (double)s[4] + c[4], (double)s[5] + c[5], n);
 }
 
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// Many curves in one persistent launch: CTAs take (curve, block of
+// kMainThreads*F frequencies) items from an atomic ticket, run the strip over
+// all samples of the curve, finish p in FP64, write P if asked and fold the
+// block's largest P into the curve's (P bits << 32 | ~k) maximum.
+template <int F, int MODE>
+__global__ void __launch_bounds__(kMainThreads)
+gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
+                 const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
+                 const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
+                 const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey) {
+    __shared__ __align__(16) TileSmemN<1> sm;
+    __shared__ int s_item;
+    __shared__ unsigned long long s_red[kMainThreads / 32];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const int64_t b = off[w.curve], e = off[w.curve + 1];
+        const int64_t N_f = nf[w.curve];
+        const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+        GStrip<F, MODE> st;
+        st.zero();
+        for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e,
+                           [&](const uint4* a, const float4* bb, const float (*qs)[kTile], int n) {
+#pragma unroll 2
+                               for (int j = 0; j < n; ++j) {
+                                   const float4 B = bb[j];
+                                   st.add(a[j], B, B.x, qs[0][j], k0);
+                               }
+                           });
+        float* P = P_out ? P_out + P_off[w.curve] : nullptr;
+        unsigned long long best = 0ull;
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
+            const uint32_t k = k0 + i;
+            if (k < (uint32_t)N_f) {
+                const float p = gls_value(st.xc[i], st.xs[i], st.c1[i], st.s1[i], st.cc[i], st.cs[i], (double)(e - b));
+                if (P) P[k] = p;
+                best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_down_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = s_red[0];
+            for (int x = 1; x < kMainThreads / 32; ++x) m = umax64(m, s_red[x]);
+            if (m) atomicMax(&maxkey[w.curve], m);
+        }
+    }
+}
+
+using GlsBatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const uint4*,
+                            const float4*, const float*, float*, const int64_t*, unsigned long long*);
+
+GlsBatchFn gls_batch_fn(int mode, int F) {
+    if (F == 16) {
+        switch (mode) {
+            case kMufu: return gls_batch_kernel<16, kMufu>;
+            case kRecur: return gls_batch_kernel<16, kRecur>;
+            case kRecur3: return gls_batch_kernel<16, kRecur3>;
+            case kRecur3x2: return gls_batch_kernel<16, kRecur3x2>;
+            default: return nullptr;
+        }
+    }
+    if (F == 8) {
+        switch (mode) {
+            case kMufu: return gls_batch_kernel<8, kMufu>;
+            case kRecur: return gls_batch_kernel<8, kRecur>;
+            case kRecur3: return gls_batch_kernel<8, kRecur3>;
+            case kRecur3x2: return gls_batch_kernel<8, kRecur3x2>;
+            default: return nullptr;
+        }
+    }
+    return nullptr;
+}
+
 using GlsFn = void (*)(const uint4*, const float4*, const float*, int64_t, int64_t, int, int64_t, float*, float*);
 
 template <int MODE>
@@ -277,6 +361,27 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
     dim3 grid((unsigned)s.nfb, (unsigned)s.split);
     fn<<<grid, kMainThreads, 0, st>>>(recA, recB, q, N, s.chunk, (int)N_f, s.nf_pad, part,
                                       s.split == 1 ? P_out : nullptr);
+    return cudaGetLastError();
+}
+
+int gls_batch_occupancy(int mode, int F) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F);
+    if (!fn) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kMainThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+                             const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
+                             const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
+                             cudaStream_t st) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F);
+    if (!fn) return cudaErrorInvalidValue;
+    fn<<<grid, kMainThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,9 @@
-// lsp_gls_api.cu -- lsp_periodogram_gls: the floating-mean (generalized,
-// weighted) periodogram of one curve (gls.cu).
+// lsp_gls_api.cu -- lsp_periodogram_gls and lsp_batch_gls: the floating-mean
+// (generalized, weighted) periodogram of one curve or of many (gls.cu).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "lsp_ctx.h"
 
@@ -118,6 +120,153 @@ lsp_status lsp_periodogram_gls(lsp_ctx* ctx, const double* t, const double* X, c
         LSP_CUDA(ctx, cudaMemcpyAsync(P_out, pd, (size_t)N_f * 4, cudaMemcpyDeviceToHost, st));
         return lsp_sync(ctx, -1.0);
     }
+    return LSP_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                         const double* dy, const double* f_0, const double* df, const int64_t* N_f, float* P_out,
+                         const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    ctx->err.clear();
+    ctx->timing_valid = false;
+    ctx->last_launches = 0;
+    if (n_curves < 1 || n_curves > 65535)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "n_curves = %d out of range [1, 65535]", n_curves);
+    if (!t_off || !t || !X || !f_0 || !df || !N_f) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
+    if (!P_out && !maxP_out && !argmax_out) return fail(ctx, LSP_ERR_INVALID_ARG, "no output requested");
+    if (P_out && !P_off) return fail(ctx, LSP_ERR_INVALID_ARG, "P_out needs P_off");
+    if (ctx->opt.phase_mode != LSP_PHASE_FIXED64)
+        return fail(ctx, LSP_ERR_UNSUPPORTED, "the floating-mean periodogram uses the fixed-point phase only");
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    lsp_status rs;
+
+    std::vector<int64_t> off, nf, poff;
+    std::vector<double> f0v, dfv;
+    if ((rs = fetch(ctx, t_off, (size_t)n_curves + 1, off)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, N_f, (size_t)n_curves, nf)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, f_0, (size_t)n_curves, f0v)) != LSP_OK) return rs;
+    if ((rs = fetch(ctx, df, (size_t)n_curves, dfv)) != LSP_OK) return rs;
+    if (P_out && (rs = fetch(ctx, P_off, (size_t)n_curves + 1, poff)) != LSP_OK) return rs;
+    if (off[0] != 0) return fail(ctx, LSP_ERR_INVALID_ARG, "t_off[0] must be 0");
+    for (int c = 0; c < n_curves; ++c) {
+        if (off[c + 1] - off[c] < 3)
+            return fail(ctx, LSP_ERR_INVALID_ARG, "curve %d has %lld samples (need >= 3)", c,
+                        (long long)(off[c + 1] - off[c]));
+        if (nf[c] < 0 || nf[c] >= (int64_t(1) << 31))
+            return fail(ctx, LSP_ERR_INVALID_ARG, "N_f[%d] = %lld out of range", c, (long long)nf[c]);
+        if (!std::isfinite(f0v[c]) || !std::isfinite(dfv[c]))
+            return fail(ctx, LSP_ERR_NONFINITE, "grid of curve %d is not finite", c);
+        if (P_out && (poff[c + 1] - poff[c] < nf[c] || poff[c] < 0))
+            return fail(ctx, LSP_ERR_INVALID_ARG, "P_off leaves fewer than N_f[%d] slots", c);
+    }
+    const int64_t total = off[n_curves];
+    const int64_t P_total = P_out ? poff[n_curves] : 0;
+
+    // the batch buffers are shared with lsp_batch: its cached work list is rebuilt next time
+    drop_plan(ctx);
+    const int64_t *d_off = nullptr, *d_nf = nullptr, *d_poff = nullptr;
+    const double *d_f0 = nullptr, *d_df = nullptr, *d_t = nullptr, *d_X = nullptr, *d_dy = nullptr;
+    if ((rs = device_view(ctx, t_off, (size_t)n_curves + 1, ctx->b_off, &d_off)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, N_f, (size_t)n_curves, ctx->b_nf, &d_nf)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, f_0, (size_t)n_curves, ctx->b_f0, &d_f0)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, df, (size_t)n_curves, ctx->b_df, &d_df)) != LSP_OK) return rs;
+    if (P_out && (rs = device_view(ctx, P_off, (size_t)n_curves + 1, ctx->b_poff, &d_poff)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, t, (size_t)total, ctx->b_t, &d_t)) != LSP_OK) return rs;
+    if ((rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
+    if (dy && (rs = device_view(ctx, dy, (size_t)total, ctx->dy_stage, &d_dy)) != LSP_OK) return rs;
+    const bool p_dev = !P_out || is_device_ptr(P_out);
+    const bool m_dev = !maxP_out || is_device_ptr(maxP_out);
+    const bool a_dev = !argmax_out || is_device_ptr(argmax_out);
+
+    // mode and strip length as for the single-curve floating-mean call
+    const MainShape shape = choose_gls_shape(ctx, 1 << 20, 1 << 24);
+    const int mode = shape.mode, F = shape.F;
+    const int64_t per_block = lsp::freqs_per_block(F);
+    std::vector<int> order(n_curves);
+    for (int c = 0; c < n_curves; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    std::vector<lsp::BatchItem> items;
+    for (int c : order) {
+        const int64_t nfb = (nf[c] + per_block - 1) / per_block;
+        for (int64_t fb = 0; fb < nfb; ++fb) items.push_back({c, 0, (int32_t)fb, 1});
+    }
+    if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
+
+    if ((rs = ensure(ctx, ctx->b_recA, (size_t)total * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_recB, (size_t)total * 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_xr, (size_t)total * 4)) != LSP_OK) return rs;  // the sqrt-weights
+    if ((rs = ensure(ctx, ctx->b_stats, sizeof(lsp::CurveStats) * (size_t)n_curves)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_head, 16)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_maxkey, (size_t)n_curves * 8)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_items, items.size() * sizeof(lsp::BatchItem) + 16)) != LSP_OK) return rs;
+    if (!p_dev && (rs = ensure(ctx, ctx->b_P, (size_t)P_total * 4)) != LSP_OK) return rs;
+    if (!m_dev && (rs = ensure(ctx, ctx->b_maxP, (size_t)n_curves * 4)) != LSP_OK) return rs;
+    if (!a_dev && (rs = ensure(ctx, ctx->b_argmax, (size_t)n_curves * 4)) != LSP_OK) return rs;
+    float* d_P = P_out ? (p_dev ? P_out : (float*)ctx->b_P.p) : nullptr;
+    float* d_maxP = maxP_out ? (m_dev ? maxP_out : (float*)ctx->b_maxP.p) : nullptr;
+    int32_t* d_argmax = argmax_out ? (a_dev ? argmax_out : (int32_t*)ctx->b_argmax.p) : nullptr;
+
+    const size_t item_bytes = items.size() * sizeof(lsp::BatchItem);
+    if ((rs = ensure_pinned(ctx, item_bytes + 64)) != LSP_OK) return rs;
+    LSP_CUDA(ctx, cudaStreamSynchronize(st));  // the pinned buffer may still feed an earlier copy
+    if (!items.empty()) {
+        std::memcpy(ctx->pinned, items.data(), item_bytes);
+        LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_items.p, ctx->pinned, item_bytes, cudaMemcpyHostToDevice, st));
+    }
+    const bool timing = ctx->opt.timing != 0;
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+    LSP_CUDA(ctx, cudaMemsetAsync(ctx->b_head.p, 0, 16, st));
+    LSP_CUDA(ctx, cudaMemsetAsync(ctx->b_maxkey.p, 0, (size_t)n_curves * 8, st));
+    lsp::CurveStats* stats = (lsp::CurveStats*)ctx->b_stats.p;
+    LSP_CUDA(ctx, lsp::launch_prep_stats(d_t, d_X, d_off, 0, n_curves, stats, ctx->status_d, nullptr, nullptr, st,
+                                         d_dy));
+    const int64_t max_n = off[order[0] + 1] - off[order[0]];
+    LSP_CUDA(ctx, lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0, stats,
+                                           (uint4*)ctx->b_recA.p, (float4*)ctx->b_recB.p, nullptr, nullptr, st,
+                                           d_dy, (float*)ctx->b_xr.p));
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+    int launches = 2;
+    if (!items.empty()) {
+        const int occ = std::max(1, lsp::gls_batch_occupancy(mode, F));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
+        LSP_CUDA(ctx, lsp::launch_gls_batch(mode, F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+                                            (unsigned*)ctx->b_head.p, d_off, d_nf, (const uint4*)ctx->b_recA.p,
+                                            (const float4*)ctx->b_recB.p, (const float*)ctx->b_xr.p, d_P, d_poff,
+                                            (unsigned long long*)ctx->b_maxkey.p, st));
+        ++launches;
+    }
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
+    if (d_maxP || d_argmax) {
+        LSP_CUDA(ctx, lsp::launch_unpack_max((const unsigned long long*)ctx->b_maxkey.p, n_curves, d_maxP, d_argmax,
+                                             st));
+        ++launches;
+    }
+    if (timing) {
+        LSP_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
+        ctx->timing_valid = true;
+        ctx->has_finalize = true;
+    }
+    ctx->last_launches = launches;
+    bool host_out = false;
+    if (P_out && !p_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(P_out, d_P, (size_t)P_total * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (maxP_out && !m_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(maxP_out, d_maxP, (size_t)n_curves * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (argmax_out && !a_dev) {
+        LSP_CUDA(ctx, cudaMemcpyAsync(argmax_out, d_argmax, (size_t)n_curves * 4, cudaMemcpyDeviceToHost, st));
+        host_out = true;
+    }
+    if (host_out) return lsp_sync(ctx, -1.0);
     return LSP_OK;
 }
 

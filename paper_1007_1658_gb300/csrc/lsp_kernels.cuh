@@ -103,6 +103,13 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
                        int64_t N_f, float* part, float* P_out, cudaStream_t st);
 cudaError_t launch_gls_finalize(const MainShape& s, const float* part, int64_t N, int64_t N_f, float* P_out,
                                 cudaStream_t st);
+struct BatchItem;
+// Many curves (CSR samples, per-curve grids) in one persistent launch; F in {8, 16}.
+int gls_batch_occupancy(int mode, int F);
+cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+                             const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
+                             const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
+                             cudaStream_t st);
 
 // ---- Press-Rybicki fast approximation (press_rybicki.cu) ----
 

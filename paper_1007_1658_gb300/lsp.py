@@ -61,6 +61,7 @@ def load():
         lib.lsp_periodogram.argtypes = [p, p, p, i64, d, d, i64, p]
         lib.lsp_periodogram_gls.argtypes = [p, p, p, p, i64, d, d, i64, p]
         lib.lsp_press_rybicki.argtypes = [p, p, p, i64, d, d, i64, i32, p]
+        lib.lsp_batch_gls.argtypes = [p, i32, p, p, p, p, p, p, p, p, p, p, p]
         lib.lsp_grid.argtypes = [d, d, i64, d, d, p, p, p]
         lib.lsp_sync.argtypes = [p, d]
         lib.lsp_last_timing.argtypes = [p, p, p, p]
@@ -227,6 +228,18 @@ class Context:
         self._check(self._lib.lsp_press_rybicki(self.h, _ptr(t), _ptr(X), int(n), float(f0), float(df), nf,
                                                 int(macc), _ptr(out)))
         return out
+
+    def batch_gls(self, t_off, t, X, f0, df, nf, dy=None, P_out=None, P_off=None, maxP=None, argmax=None):
+        """lsp_batch_gls: floating-mean periodograms of many curves (CSR t_off/t/X/dy,
+        per-curve grids).  A missing maxP/argmax is allocated like t and returned."""
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        if maxP is None and argmax is None and P_out is None:
+            maxP = _like(t, (n,), np.float32)
+            argmax = _like(t, (n,), np.int32)
+        self._bind_stream()
+        self._check(self._lib.lsp_batch_gls(self.h, n, _ptr(t_off), _ptr(t), _ptr(X), _ptr(dy), _ptr(f0), _ptr(df),
+                                            _ptr(nf), _ptr(P_out), _ptr(P_off), _ptr(maxP), _ptr(argmax)))
+        return maxP, argmax
 
     def batch(self, t_off, t, f0, df, nf, X=None, seed=0, n_real=1, P_out=None, P_off=None,
               maxP=None, argmax=None):

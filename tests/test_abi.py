@@ -35,7 +35,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for must in ("lsp_create", "lsp_periodogram", "lsp_batch", "lsp_fap_predict", "lsp_destroy", "lsp_sync",
                  "lsp_grid", "lsp_last_error", "lsp_noise", "lsp_fap_train_step", "lsp_periodogram_noalloc",
-                 "lsp_periodogram_gls", "lsp_press_rybicki"):
+                 "lsp_periodogram_gls", "lsp_press_rybicki", "lsp_batch_gls"):
         assert must in names, must
 
 

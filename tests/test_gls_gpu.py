@@ -193,3 +193,61 @@ def test_noise_power_follows_the_exact_beta_law(ctx):
         X = 4.0 + dy * rng.normal(size=n)
         z[r] = 2 * float(ctx.periodogram_gls(t, X, 1.37, 1.0, 1, dy=dy)[0]) / n
     assert stats.kstest(z, stats.beta(1, (n - 3) / 2).cdf).pvalue > 1e-3
+
+
+def _err_batch(n_curves=9, seed=41):
+    from paper_1007_1658_gb300 import synth
+    b = synth.noise_batch(n_curves=n_curves, seed=seed, nt_min=30, nt_max=1500, t_min=5.0, t_max=60.0)
+    rng = np.random.default_rng(seed)
+    dy = rng.uniform(0.3, 3.0, b.t.size)
+    X = 7.0 + dy * rng.normal(size=b.t.size)
+    for c in range(b.n):  # a line in every curve
+        s = slice(b.t_off[c], b.t_off[c + 1])
+        X[s] += 1.5 * np.sin(2 * np.pi * (0.4 + 0.07 * c) * b.t[s])
+    return b, X, dy
+
+
+@pytest.mark.parametrize("weighted", [True, False])
+def test_batch_matches_the_oracle_curve_by_curve(ctx, lsp, weighted):
+    b, X, dy = _err_batch()
+    d = dy if weighted else None
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    P = np.empty(int(P_off[-1]), np.float32)
+    mx = np.empty(b.n, np.float32)
+    am = np.empty(b.n, np.int32)
+    ctx.set_options()
+    ctx.batch_gls(b.t_off, b.t, X, b.f0, b.df, b.nf, dy=d, P_out=P, P_off=P_off, maxP=mx, argmax=am)
+    for c in range(b.n):
+        s = slice(b.t_off[c], b.t_off[c + 1])
+        ref = oracle.gls_at(b.t[s], X[s], _grid(b.f0[c], b.df[c], b.nf[c]), None if d is None else d[s])
+        got = P[P_off[c]:P_off[c + 1]].astype(np.float64)
+        assert_parity(got, ref, what="batch curve %d" % c)
+        assert mx[c] == P[P_off[c] + am[c]] and mx[c] == P[P_off[c]:P_off[c + 1]].max()
+    # the single-curve entry point gives the same values
+    c = 3
+    s = slice(b.t_off[c], b.t_off[c + 1])
+    one = ctx.periodogram_gls(b.t[s], X[s], b.f0[c], b.df[c], b.nf[c], dy=None if d is None else d[s])
+    assert np.max(np.abs(one - P[P_off[c]:P_off[c + 1]])) <= 1e-5 * one.max()
+
+
+def test_batch_device_pointers_and_errors(ctx, lsp):
+    b, X, dy = _err_batch(n_curves=5, seed=7)
+    mx, am = ctx.batch_gls(torch.from_numpy(b.t_off).cuda(), _dev(b.t), _dev(X), _dev(b.f0), _dev(b.df),
+                           torch.from_numpy(b.nf).cuda(), dy=_dev(dy))
+    ctx.sync(30.0)
+    mh, ah = ctx.batch_gls(b.t_off, b.t, X, b.f0, b.df, b.nf, dy=dy)
+    assert np.array_equal(mx.cpu().numpy(), mh) and np.array_equal(am.cpu().numpy(), ah)
+    bad = dy.copy()
+    bad[3] = -1.0
+    with pytest.raises(lsp.LspError) as e:
+        ctx.batch_gls(b.t_off, b.t, X, b.f0, b.df, b.nf, dy=bad)
+    assert e.value.status == lsp.ERR_INVALID_ARG
+    off2 = b.t_off.copy()
+    off2[1] = 2  # a 2-sample curve
+    with pytest.raises(lsp.LspError) as e:
+        ctx.batch_gls(off2, b.t, X, b.f0, b.df, b.nf, dy=dy)
+    assert e.value.status == lsp.ERR_INVALID_ARG
+    # the plain batch still works on the same context afterwards
+    m2, a2 = ctx.batch(b.t_off, b.t, b.f0, b.df, b.nf, X=X)
+    assert np.all(np.isfinite(m2)) and np.all(a2 >= 0)
