@@ -429,8 +429,24 @@ def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
     peak = roof[1] * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
     kernel = "gls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode])
+    # many curves: the Monte-Carlo batch's 4096 sampling patterns as measured curves with errors
+    b = synth.noise_batch(n_curves=args.batch_curves)
+    rng = np.random.default_rng(17)
+    bdy = np.exp(rng.uniform(np.log(0.3), np.log(3.0), b.t.size))
+    bX = 5.0 + bdy * rng.normal(size=b.t.size)
+    bargs = (d(b.t_off), d(b.t), d(bX), d(b.f0), d(b.df), d(b.nf))
+    bmax = torch.empty(b.n, dtype=torch.float32, device=dev)
+    barg = torch.empty(b.n, dtype=torch.int32, device=dev)
+    bctx = lsp.Context(dev.index or 0, stream=stream)
+    dy_b = d(bdy)
+    bfn = lambda: bctx.batch_gls(*bargs, dy=dy_b, maxP=bmax, argmax=barg)
+    b_ms = _time_calls(torch, stream, bfn, 2, 3, flush)
+    bctx.close()
+    batch_line = {"workload": "%d noise_batch patterns as measured curves with errors, N_f = 2 N_t" % b.n,
+                  "ms": b_ms, "curves_per_s": b.n / (b_ms * 1e-3), "terms_per_s": b.terms / (b_ms * 1e-3)}
     return {"workload": "gapped_100k with per-sample errors (dy log-U[0.15, 1.5], 2%% x10), N_t = %d, N_f = %d"
                         % (c.t.size, c.nf),
+            "batch": batch_line,
             "ms_per_call": step_ms, "terms_per_s": terms / (step_ms * 1e-3),
             "roofline": {"bound": "alu", "kernel": kernel,
                          "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gterms/s", "frac": achieved / peak,
