@@ -138,8 +138,8 @@ lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64
  * finite nonzero FP32 number (about 1e-19 < dy < 1e19: the weights are formed
  * in FP32, summed in FP64).  N_t >= 3.
  * sincos_mode selects MUFU, RECUR, RECUR3 or RECUR3_X2 (AUTO: RECUR3_X2);
- * strips are 8 or 16 frequencies (freqs_per_thread 8 or 16; other values use
- * 16, 8 for MUFU).
+ * strips are 8, 12 or 16 frequencies (freqs_per_thread 8, 12 or 16; other
+ * values use 16, 8 for MUFU).
  * Errors: INVALID_ARG (also a bad dy, on the device), NONFINITE, DEGENERATE,
  * UNSUPPORTED (phase_mode NAIVE_FP32), OOM, CUDA.
  */

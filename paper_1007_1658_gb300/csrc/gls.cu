@@ -326,6 +326,7 @@ template <int MODE>
 GlsFn gls_fn_f(int F) {
     switch (F) {
         case 8: return gls_main_kernel<8, MODE>;
+        case 12: return gls_main_kernel<12, MODE>;
         case 16: return gls_main_kernel<16, MODE>;
         default: return nullptr;
     }

@@ -15,7 +15,8 @@ namespace {
 
 // Mode from the options (AUTO = the three-term recurrence in packed FP32x2
 // form, measured fastest for six sums per frequency); strips are 16
-// (recurrences) or 8 (MUFU) frequencies long unless 8 or 16 is asked for.
+// (recurrences) or 8 (MUFU) frequencies long unless 8, 12 or 16 is asked for
+// (12 measured equal to 16, 8 slower).
 MainShape choose_gls_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
     const lsp_options& o = ctx->opt;
@@ -32,7 +33,7 @@ MainShape choose_gls_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
         s.mode = lsp::kModeRecur3x2;
         s.F = 16;
     }
-    if (o.freqs_per_thread == 8 || o.freqs_per_thread == 16) s.F = o.freqs_per_thread;
+    if (o.freqs_per_thread == 8 || o.freqs_per_thread == 12 || o.freqs_per_thread == 16) s.F = o.freqs_per_thread;
     finish_shape(ctx, s, lsp::gls_occupancy(s.mode, s.F), N, N_f, o.split);
     return s;
 }

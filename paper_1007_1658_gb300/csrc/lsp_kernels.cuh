@@ -96,7 +96,7 @@ cudaError_t launch_finalize(const MainShape& s, const float* part, int64_t N, in
 // ---- floating-mean periodogram (gls.cu) ----
 
 // Six partial-sum rows per chunk (XC, XS, C, S, CC', CS'); q holds sqrt(w_j).
-// Strip lengths 8 and 16; modes MUFU, RECUR, RECUR3 and RECUR3 x2 (packed).
+// Strip lengths 8, 12 and 16; modes MUFU, RECUR, RECUR3 and RECUR3 x2 (packed).
 constexpr int kGlsRows = 6;
 int gls_occupancy(int mode, int F);
 cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB, const float* q, int64_t N,
