@@ -53,6 +53,7 @@ def _grid(f0, df, nf):
 
 OPTS = [dict(sincos_mode=3), dict(sincos_mode=2), dict(sincos_mode=1), dict(sincos_mode=4),
         dict(sincos_mode=3, freqs_per_thread=8), dict(sincos_mode=4, freqs_per_thread=8),
+        dict(sincos_mode=4, freqs_per_thread=12),
         dict(sincos_mode=1, freqs_per_thread=16), dict(sincos_mode=3, split=1), dict(sincos_mode=3, split=5)]
 
 
