@@ -57,10 +57,13 @@ typedef enum lsp_sincos_mode {
     LSP_SINCOS_RECUR3 = 3, /* SFU seed, one rotation, then the three-term form
                               z_{k+1} = 2 cos(2 pi t_j df) z_k - z_{k-1} (half the FMA work
                               of RECUR; error grows faster with the strip length)      */
-    LSP_SINCOS_RECUR3_X2 = 4 /* RECUR3 with the (cos, sin) pair in packed FP32x2 FMA:
-                              the same roundings (bit-identical results), fewer
-                              instructions per term; the multi-realization batch
-                              kernels use the scalar form                              */
+    LSP_SINCOS_RECUR3_X2 = 4 /* RECUR3 in packed FP32x2 FMA, the same roundings with
+                              fewer instructions per term: the classic kernels put
+                              the two halves of each strip in the two lanes (results
+                              bit-identical to RECUR3 with strips of half the length),
+                              the floating-mean kernels the (cos, sin) pair
+                              (bit-identical to RECUR3 at the same length); the
+                              multi-realization batch kernels use the scalar form    */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */

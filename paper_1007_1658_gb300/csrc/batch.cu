@@ -60,7 +60,9 @@ __device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, in
     for (int i = 0; i < FF; ++i) {
         const uint32_t k = k0 + i;
         if (k < (uint32_t)N_f) {
-            const float p = periodogram_value(st.xc[i], st.xs[i], st.cc[i], st.cs[i], n);
+            float xc, xs, cc, cs;
+            st.get(i, xc, xs, cc, cs);
+            const float p = periodogram_value(xc, xs, cc, cs, n);
             if (P) P[k] = p;
             best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
         }

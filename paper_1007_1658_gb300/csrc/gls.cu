@@ -95,9 +95,11 @@ struct GStrip {
     }
 };
 
-// Packed form of the three-term strip (see Strip<F, kRecur3x2>): the pairs
-// (XC, XS) and (C, S) take one FFMA2 each per term with the data factors +-x
-// and +-q, CC' and CS' two scalar FFMA, the recurrence one FFMA2.
+// Packed form of the three-term strip with the sign-folded y_i of
+// Strip<F, kRecur3x2>, here with the (cos, sin) pair in the two lanes: the
+// pairs (XC, XS) and (C, S) take one FFMA2 each per term with the data
+// factors +-x and +-q, CC' and CS' two scalar FFMA, the recurrence one FFMA2.
+// Bit-identical to GStrip<F, kRecur3>.
 template <int F>
 struct GStrip<F, kRecur3x2> {
     float xc[F], xs[F], c1[F], s1[F], cc[F], cs[F];

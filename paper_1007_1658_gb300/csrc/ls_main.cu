@@ -32,8 +32,9 @@
 //             identity, z_{k+1} = 2 cos(2 pi u_j) z_k - z_{k-1}: 2 FMA-pipe ops
 //             per term.  Its rounding error grows like F^2 ulp, and like
 //             F ulp / sin(2 pi u_j) for samples whose step angle is near 0 or pi.
-//   RECUR3 x2 -- the same arithmetic with the (cos, sin) pair in packed FP32x2
-//             FMA (FFMA2): fewer issue slots per term, bit-identical sums.
+//   RECUR3 x2 -- the same arithmetic in packed FP32x2 FMA (FFMA2), the two
+//             halves of the strip in the two lanes: half the issue slots per
+//             term; sums bit-identical to RECUR3 with strips of F/2.
 // NAIVE_FP32 -- the paper's own single-precision phase f*t - rintf(f*t)
 //             (Sec. 4.3), kept as a comparator.
 #include "ls_device.cuh"
@@ -82,7 +83,10 @@ ls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, 
                                  st.add(a[j], B, B.x, k0);
                              }
                          });
-    write_out<F>(st.xc, st.xs, st.cc, st.cs, k0, N_f, nf_pad, N, part, P_out);
+    float xc[F], xs[F], cc[F], cs[F];
+#pragma unroll
+    for (int i = 0; i < F; ++i) st.get(i, xc[i], xs[i], cc[i], cs[i]);
+    write_out<F>(xc, xs, cc, cs, k0, N_f, nf_pad, N, part, P_out);
 }
 
 // The paper's single-precision phase (Sec. 4.3): f_k = (float)(f0 + k df),
