@@ -222,18 +222,7 @@ gls_finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, i
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N_f) return;
     float s[kGlsSums], c[kGlsSums];
-#pragma unroll
-    for (int r = 0; r < kGlsSums; ++r) s[r] = c[r] = 0.f;
-    for (int sp = 0; sp < split; ++sp) {
-        const float* p = part + (size_t)sp * kGlsSums * (size_t)nf_pad + k;
-#pragma unroll
-        for (int r = 0; r < kGlsSums; ++r) {
-            const float v = p[(size_t)r * nf_pad];
-            const float t = s[r] + v;
-            c[r] += fabsf(s[r]) >= fabsf(v) ? (s[r] - t) + v : (v - t) + s[r];
-            s[r] = t;
-        }
-    }
+    merge_chunks<kGlsSums>(part, split, nf_pad, k, s, c);
     P_out[k] = gls_value((double)s[0] + c[0], (double)s[1] + c[1], (double)s[2] + c[2], (double)s[3] + c[3],
                          (double)s[4] + c[4], (double)s[5] + c[5], n);
 }

@@ -62,6 +62,40 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+// Fixed-order compensated (Neumaier) FP32 sum, over the `split` sample
+// chunks, of the R partial sums of frequency k (row r of chunk sp at
+// part[(sp R + r) nf_pad + k]); leaves the sums in s and their corrections in
+// c.  The loads of 8 chunks are issued before any of them is added, so a
+// thread waits on memory once per 8 chunks instead of once per chunk; the
+// additions keep the chunk order, so the result does not depend on that.
+template <int R>
+__device__ __forceinline__ void merge_chunks(const float* __restrict__ part, int split, int64_t nf_pad, int k,
+                                             float (&s)[R], float (&c)[R]) {
+    constexpr int kB = 8;
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[r] = c[r] = 0.f;
+    for (int sp0 = 0; sp0 < split; sp0 += kB) {
+        float v[kB][R];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                v[u][r] = sp0 + u < split ? part[((size_t)(sp0 + u) * R + r) * (size_t)nf_pad + k] : 0.f;
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+            if (sp0 + u < split) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float x = v[u][r];
+                    const float t = s[r] + x;
+                    c[r] += fabsf(s[r]) >= fabsf(x) ? (s[r] - t) + x : (x - t) + s[r];
+                    s[r] = t;
+                }
+            }
+        }
+    }
+}
+
 // Eq. 5 with tau from Eq. 6, in closed form.  With A = CC - SS = 2CC - N,
 // B = 2CS and R = |A + iB| = |sum exp(2 i w t_j)|, tan 2wtau = B/A gives
 // cos 2wtau = A/R, sin 2wtau = B/R, and the two denominators of Eq. 5 are

@@ -151,20 +151,8 @@ finalize_kernel(const float* __restrict__ part, int split, int64_t nf_pad, int N
                 float* __restrict__ P_out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N_f) return;
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int sp = 0; sp < split; ++sp) {
-        const float* p = part + (size_t)sp * 4 * (size_t)nf_pad + k;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float v = p[(size_t)q * nf_pad];
-            const float tsum = s[q] + v;
-            if (fabsf(s[q]) >= fabsf(v))
-                c[q] += (s[q] - tsum) + v;
-            else
-                c[q] += (v - tsum) + s[q];
-            s[q] = tsum;
-        }
-    }
+    float s[4], c[4];
+    merge_chunks<4>(part, split, nf_pad, k, s, c);
     P_out[k] = periodogram_value(s[0] + c[0], s[1] + c[1], s[2] + c[2], s[3] + c[3], n);
 }
 

@@ -61,10 +61,9 @@ void lsp::host::default_mode_F(const lsp_options& o, int* mode, int* F) {
 }
 
 // Launch shape: mode, strip length F, N_t split.  The split is chosen so the
-// grid fills whole waves of resident CTAs while every chunk keeps at least
-// one tile of samples (chunks below a tile measured slower: the extra
-// partial sums cost more than the parallelism gains); small problems get
-// shorter strips instead.
+// grid fills whole waves of resident CTAs, with chunks of at least kMinChunk
+// samples; problems that still leave the GPU short of one wave get shorter
+// strips as well.
 MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
     MainShape s{};
     lsp_options o = ctx->opt;
@@ -74,16 +73,16 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
         if (const TuneEntry* te = tuned(ctx, N, N_f)) {
             o.sincos_mode = te->sincos;
             o.freqs_per_thread = te->F;
-            o.split = (int)std::min<int64_t>(te->split, std::max<int64_t>(1, N / lsp::kTile));
+            o.split = (int)std::min<int64_t>(te->split, std::max<int64_t>(1, N / lsp::kMinChunk));
         }
     }
     default_mode_F(o, &s.mode, &s.F);
     if (o.freqs_per_thread) {
         s.F = o.freqs_per_thread;
     } else if (s.mode != lsp::kModeNaive) {
-        // small problems: shorter strips until the grid (at one tile of samples
-        // per chunk) fills a wave of resident CTAs, down to 4 frequencies
-        const int64_t max_split = std::max<int64_t>(1, N / lsp::kTile);
+        // small problems: shorter strips until the grid (at the shortest
+        // chunks) fills a wave of resident CTAs, down to 4 frequencies
+        const int64_t max_split = std::max<int64_t>(1, N / lsp::kMinChunk);
         for (int f : {24, 16, 8, 4}) {
             if (f > s.F) continue;
             s.F = f;
@@ -105,14 +104,16 @@ void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64
     if (split <= 0) {
         const int occ = std::max(1, occ_in);
         const int64_t slots = (int64_t)occ * std::max(1, ctx->sms);
-        const int64_t max_split = std::max<int64_t>(1, N / lsp::kTile);
+        const int64_t max_split = std::max<int64_t>(1, N / lsp::kMinChunk);
         double best = -1.0;
         int best_s = 1;
         for (int64_t sp = 1; sp <= std::min<int64_t>(max_split, 256); ++sp) {
             const int64_t ctas = (int64_t)s.nfb * sp;
             const int64_t waves = (ctas + slots - 1) / slots;
-            // fraction of SM slots busy over the run, slightly favouring fewer splits
-            const double eff = (double)ctas / (double)(waves * slots) - 0.002 * (double)sp;
+            // fraction of SM slots busy over the run, slightly favouring fewer
+            // splits (a relative penalty, so a grid far below one wave still
+            // takes every split it can)
+            const double eff = (double)ctas / (double)(waves * slots) * (1.0 - 0.002 * (double)sp);
             if (eff > best + 1e-9) {
                 best = eff;
                 best_s = (int)sp;

@@ -79,6 +79,11 @@ struct MainShape {
 
 constexpr int kMainThreads = 128;
 constexpr int kTile = 256;
+// Fewest samples per N_t chunk that the launch-shape heuristic makes.  A
+// problem too small to fill one wave of CTAs is latency-bound: each thread's
+// serial loop over its chunk is the critical path, so such problems are split
+// down to chunks of this many samples (a quarter of a tile).
+constexpr int kMinChunk = 64;
 
 // Frequencies covered by one CTA of the main kernel.
 inline int freqs_per_block(int F) { return kMainThreads * F; }

@@ -104,7 +104,7 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     const int occ = lsp::main_occupancy(s.mode, s.F);
     const int64_t slots = (int64_t)occ * (sms > 0 ? sms : 1);
     int64_t split = (slots + s.nfb - 1) / s.nfb;
-    split = std::min<int64_t>(split, std::max<int64_t>(1, N_t / lsp::kTile));
+    split = std::min<int64_t>(split, std::max<int64_t>(1, N_t / lsp::kMinChunk));
     split = std::min<int64_t>(split, fit);
     if (split < 2) split = 1;
     s.chunk = (N_t + split - 1) / split;

@@ -114,7 +114,7 @@ extern "C" lsp_status lsp_autotune(lsp_ctx* ctx, int64_t N_t, int64_t N_f, lsp_o
         ctx->opt.freqs_per_thread = c.F;
         ctx->opt.split = 0;
         const int base_split = choose_shape(ctx, N_t, N_f).split;
-        const int max_split = (int)std::max<int64_t>(base_split, std::max<int64_t>(1, N_t / lsp::kTile));
+        const int max_split = (int)std::max<int64_t>(base_split, std::max<int64_t>(1, N_t / lsp::kMinChunk));
         const int splits[3] = {base_split, std::max(1, base_split / 2), std::min<int>(base_split * 2, max_split)};
         for (int si = 0; si < 3; ++si) {
             if (si > 0 && splits[si] == base_split) continue;
