@@ -333,3 +333,47 @@ def test_packed_recurrence_is_bit_identical_to_scalar(ctx, F):
         for split in (1, 6):
             outs.append(_run(ctx, c.t, c.X, c.f0, c.df, nf, sincos_mode=mode, freqs_per_thread=f, split=split))
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+
+
+@pytest.mark.parametrize("kind", ["classic", "floating_mean"])
+def test_largest_accepted_grid(ctx, kind):
+    """The largest grid the library accepts, N_f = 2^31 - 1 (frequency index
+    k up to 2^31 - 2 in the fixed-point phase and the output address), on a
+    ragged 97-sample curve: sampled bins at both ends, across the last strip
+    and block boundaries and at random, against the oracle one by one; the
+    whole output finite and in [0, N_t/2].  N_f = 2^31 is refused before any
+    launch."""
+    rng = np.random.default_rng(31)
+    n = 97
+    t = np.sort(rng.uniform(0.0, 50.0, n)) + 3.0
+    X = np.sin(2 * np.pi * 1.7 * t) + rng.normal(size=n)
+    dy = rng.uniform(0.5, 1.5, n)
+    df = 1.0 / (4.0 * (t.max() - t.min()))
+    nf = (1 << 31) - 1
+    P = torch.empty(1 << 31, dtype=torch.float32, device="cuda")
+    ctx.set_options()
+    if kind == "classic":
+        ctx.periodogram(_dev(t), _dev(X), df, df, nf, out=P)
+    else:
+        ctx.periodogram_gls(_dev(t), _dev(X), df, df, nf, dy=_dev(dy), out=P)
+    ctx.sync(120.0)
+    Pv = P[:nf]
+    assert bool(torch.isfinite(Pv).all())
+    assert float(Pv.min()) >= 0.0 and float(Pv.max()) <= n / 2 * (1 + 1e-4)
+    ks = set(range(8)) | set(range(nf - 8, nf))
+    for m in (1, 2, 3, 97):
+        top = nf - (nf % 3072) - 3072 * (m - 1)
+        ks |= set(range(top - 3, top + 3))
+    ks |= set(rng.integers(0, nf, 64).tolist())
+    ks = np.array(sorted(k for k in ks if 0 <= k < nf), dtype=np.int64)
+    got = P[torch.from_numpy(ks).cuda()].cpu().numpy().astype(np.float64)
+    freqs = df + ks * df
+    ref = oracle.periodogram_at(t, X, freqs) if kind == "classic" else oracle.gls_at(t, X, freqs, dy)
+    assert_parity(got, ref, peaks=np.argsort(ref)[-10:], what="N_f = 2^31 - 1, %s" % kind)
+    with pytest.raises(Exception):
+        if kind == "classic":
+            ctx.periodogram(_dev(t), _dev(X), df, df, 1 << 31, out=P)
+        else:
+            ctx.periodogram_gls(_dev(t), _dev(X), df, df, 1 << 31, dy=_dev(dy), out=P)
+    del P, Pv
+    torch.cuda.empty_cache()
