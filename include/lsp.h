@@ -81,7 +81,8 @@ typedef struct lsp_options {
                                  or 20|28 with the recurrences; multi-realization
                                  batches take it when their kernels have that shape
                                  (12 with 4 realizations, 16 with 2)                    */
-    int32_t split;            /* N_t-splits per frequency block: 0 = auto, else >= 1    */
+    int32_t split;            /* N_t-splits per frequency block: 0 = auto (chunks of
+                                 64 .. 65,536 samples), else 1 .. 65535                 */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */
     int32_t batch_rhs;        /* lsp_batch with n_real > 1: realizations sharing one pass
@@ -208,9 +209,12 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 4)
  * share each pass over a curve's samples: the phase, the sin/cos recurrence
  * and CC, CS are computed once for the group and only XC, XS per realization
- * (strips of 8, 8, 4 frequencies for R = 2, 4, 8), which halves the
+ * (strips of 16, 12, 4 frequencies for R = 2, 4, 8), which halves the
  * arithmetic per periodogram; each (frequency, realization) is computed
  * exactly as the one-at-a-time kernel with the same strip length would.
+ * A work item sums over all samples of its curve in FP32 (the batch does not
+ * split N_t), so curves far beyond 10^6 samples are better served by
+ * lsp_periodogram, which bounds each running sum to 65,536 samples.
  * At least one output must be given.  Arrays may be host or device pointers
  * (metadata is read on the host in either case); the sin/cos mode and strip
  * length follow the context's options (the naive FP32 phase is not offered).

@@ -27,7 +27,8 @@ lsp_status check_options(lsp_ctx* ctx, const lsp_options* o) {
         return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread must be 0, 4, 8, 12, 16, 20, 24 or 28");
     if ((F == 20 || F == 28) && (o->sincos_mode == LSP_SINCOS_MUFU || o->phase_mode == LSP_PHASE_NAIVE_FP32))
         return fail(ctx, LSP_ERR_INVALID_ARG, "freqs_per_thread 20 and 28 are recurrence-only");
-    if (o->split < 0) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be >= 0");
+    // the split is the grid's second dimension
+    if (o->split < 0 || o->split > 65535) return fail(ctx, LSP_ERR_INVALID_ARG, "split must be in [0, 65535]");
     if (o->batch_rhs != 0 && o->batch_rhs != 1 && o->batch_rhs != 2 && o->batch_rhs != 4 && o->batch_rhs != 8)
         return fail(ctx, LSP_ERR_INVALID_ARG, "batch_rhs must be 0, 1, 2, 4 or 8");
     for (int i = 0; i < 5; ++i)
@@ -105,21 +106,24 @@ void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64
         const int occ = std::max(1, occ_in);
         const int64_t slots = (int64_t)occ * std::max(1, ctx->sms);
         const int64_t max_split = std::max<int64_t>(1, N / lsp::kMinChunk);
+        // at most kMaxChunk samples per chunk, then up to 255 more splits
+        const int64_t lo = std::min<int64_t>(65535, std::max<int64_t>(1, (N + lsp::kMaxChunk - 1) / lsp::kMaxChunk));
+        const int64_t hi = std::min<int64_t>(65535, std::max<int64_t>(lo, std::min<int64_t>(max_split, lo + 255)));
         double best = -1.0;
-        int best_s = 1;
-        for (int64_t sp = 1; sp <= std::min<int64_t>(max_split, 256); ++sp) {
+        int64_t best_s = lo;
+        for (int64_t sp = lo; sp <= hi; ++sp) {
             const int64_t ctas = (int64_t)s.nfb * sp;
             const int64_t waves = (ctas + slots - 1) / slots;
             // fraction of SM slots busy over the run, slightly favouring fewer
             // splits (a relative penalty, so a grid far below one wave still
             // takes every split it can)
-            const double eff = (double)ctas / (double)(waves * slots) * (1.0 - 0.002 * (double)sp);
+            const double eff = (double)ctas / (double)(waves * slots) / (1.0 + 0.002 * (double)(sp - lo));
             if (eff > best + 1e-9) {
                 best = eff;
-                best_s = (int)sp;
+                best_s = sp;
             }
         }
-        split = best_s;
+        split = (int)best_s;
     }
     if (split > N) split = (int)std::max<int64_t>(1, N);
     s.chunk = (N + split - 1) / split;

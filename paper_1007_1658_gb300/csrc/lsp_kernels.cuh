@@ -84,6 +84,12 @@ constexpr int kTile = 256;
 // serial loop over its chunk is the critical path, so such problems are split
 // down to chunks of this many samples (a quarter of a tile).
 constexpr int kMinChunk = 64;
+// Most samples per N_t chunk that the launch-shape heuristic makes.  Each
+// thread's FP32 running sums cover one chunk (the paper's chunked summation,
+// Sec. 4.2, at a coarser grain) and the chunks are merged with compensated
+// sums, so the rounding error of a sum stays near that of 65,536 terms
+// however large N_t grows.
+constexpr int64_t kMaxChunk = int64_t(1) << 16;
 
 // Frequencies covered by one CTA of the main kernel.
 inline int freqs_per_block(int F) { return kMainThreads * F; }

@@ -92,8 +92,8 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     float* part = (float*)(base + kHeaderBytes + kRecordBytes);
 
     // Launch shape of the default (three-term recurrence) path: strips of 24
-    // frequencies; the N_t split fills the SMs but never needs more partial
-    // sums than fit.
+    // frequencies; the N_t split fills the SMs and keeps chunks within
+    // kMaxChunk samples, but never needs more partial sums than fit.
     lsp::MainShape s{};
     s.mode = lsp::kModeRecur3;
     s.F = 24;
@@ -105,6 +105,7 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     const int64_t slots = (int64_t)occ * (sms > 0 ? sms : 1);
     int64_t split = (slots + s.nfb - 1) / s.nfb;
     split = std::min<int64_t>(split, std::max<int64_t>(1, N_t / lsp::kMinChunk));
+    split = std::max<int64_t>(split, (N_t + lsp::kMaxChunk - 1) / lsp::kMaxChunk);
     split = std::min<int64_t>(split, fit);
     if (split < 2) split = 1;
     s.chunk = (N_t + split - 1) / split;
