@@ -281,6 +281,8 @@ def run_gpu(args, rank, world, dist):
                     "note": "prep + main (+ finalize), device pointers, median of 20"},
         "clocks": clk.summary(),
     }
+    if args.probe:
+        line["pipe_rates"] = pipe_rates(ctx, sms, peaks["sm_max_mhz"])
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(c, args.cpu_bins).items() if k != "seconds"}
     if args.batch:
@@ -295,6 +297,18 @@ def run_gpu(args, rank, world, dist):
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def pipe_rates(ctx, sms, sm_max_mhz):
+    """lsp_probe_pipes on this GPU (after the timed region): the measured
+    per-SM, per-clock rates behind the roofline denominators, and the roofs
+    they imply for each sin/cos mode at the SM count and maximum clock."""
+    r = ctx.probe_pipes()
+    g = sms * sm_max_mhz * 1e6 / 1e9
+    r["implied_roof_Gterms"] = {"MUFU (1 sin/cos pair per term)": r["sincos_per_clk_sm"] * g,
+                                "RECUR (8 FMA-pipe ops per term)": r["ffma_per_clk_sm"] / 8 * g,
+                                "RECUR3 (6 FMA-pipe ops per term)": r["ffma_per_clk_sm"] / 6 * g}
+    return r
 
 
 def _e2e(lsp, torch, c, f0, local, stream, args, world):
@@ -591,6 +605,7 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-gls", dest="gls", action="store_false", help="skip the floating-mean periodogram leg")
     ap.add_argument("--no-paper", dest="paper", action="store_false", help="skip the paper-shape N_t sweep")
+    ap.add_argument("--no-probe", dest="probe", action="store_false", help="skip the pipe-rate probe")
     ap.add_argument("--nf", type=int, default=0, help="override N_f (smaller profiling case)")
     ap.add_argument("--batch-curves", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=3)

@@ -256,6 +256,31 @@ lsp_status lsp_grid(double t_min, double t_max, int64_t N_t, double F_over, doub
 lsp_status lsp_autotune(lsp_ctx *ctx, int64_t N_t, int64_t N_f, lsp_options *chosen);
 
 /*
+ * Pipe-rate probe: the per-SM, per-clock rates of the operations the
+ * periodogram kernels are built from, measured on the context's GPU (Sec. 5.3
+ * puts the GPU's lead down to its sin/cos throughput; these are the
+ * denominators of the kernels' rooflines).  Each rate comes from one launch
+ * of independent dependency chains on 4 CTAs of 256 threads per SM, timed
+ * with clock64 (slowest CTA) after one untimed launch.
+ */
+typedef struct lsp_pipe_rates {
+    int32_t sms;                   /* streaming multiprocessors                        */
+    double sm_mhz;                 /* SM clock during the FMA probe: its cycles over its
+                                      CUDA-event time (a little low: the event also
+                                      spans the launch)                               */
+    double sincos_per_clk_sm;      /* __sincosf pairs (2 SFU ops each) per clock per SM */
+    double ffma_per_clk_sm;        /* FP32 FMA per clock per SM                        */
+    double ffma2_lanes_per_clk_sm; /* lanes of packed FP32x2 FMA per clock per SM      */
+} lsp_pipe_rates;
+
+/*
+ * Runs the probe on the context's stream and blocks until it is done;
+ * allocates and frees its own small buffers (so it synchronizes the device).
+ * out: host struct, filled on success.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+lsp_status lsp_probe_pipes(lsp_ctx *ctx, lsp_pipe_rates *out);
+
+/*
  * Wait for the context's queued work, at most `timeout_s` seconds (< 0: no
  * limit), polling a CUDA event.  Returns TIMEOUT if the deadline passes (the
  * work stays queued), else the first device-detected data error of the calls

@@ -43,6 +43,11 @@ class lsp_options(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 5)]
 
 
+class lsp_pipe_rates(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int32), ("sm_mhz", ctypes.c_double), ("sincos_per_clk_sm", ctypes.c_double),
+                ("ffma_per_clk_sm", ctypes.c_double), ("ffma2_lanes_per_clk_sm", ctypes.c_double)]
+
+
 def load():
     """Open liblsp.so (raises if it is missing: build it with __graft_entry__.build())."""
     global _lib
@@ -105,6 +110,9 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_autotune"):
         lib.lsp_autotune.argtypes = [p, i64, i64, ctypes.POINTER(lsp_options)]
         lib.lsp_autotune.restype = ctypes.c_int
+    if hasattr(lib, "lsp_probe_pipes"):
+        lib.lsp_probe_pipes.argtypes = [p, ctypes.POINTER(lsp_pipe_rates)]
+        lib.lsp_probe_pipes.restype = ctypes.c_int
     if hasattr(lib, "lsp_noise"):
         lib.lsp_noise.argtypes = [p, u64, i32, i32, i64, p]
         lib.lsp_noise.restype = ctypes.c_int
@@ -275,6 +283,13 @@ class Context:
         self._bind_stream()
         self._check(self._lib.lsp_autotune(self.h, int(n_t), int(n_f), ctypes.byref(o)))
         return {"sincos_mode": o.sincos_mode, "freqs_per_thread": o.freqs_per_thread, "split": o.split}
+
+    def probe_pipes(self):
+        """lsp_probe_pipes: measured per-SM, per-clock pipe rates as a dict."""
+        r = lsp_pipe_rates()
+        self._bind_stream()
+        self._check(self._lib.lsp_probe_pipes(self.h, ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in lsp_pipe_rates._fields_}
 
     # ---- learned false-alarm surrogate ----
     def fap_features(self, t_off, t, f0, df, nf, out=None):
