@@ -82,7 +82,7 @@ typedef struct lsp_options {
                                  batches take it when their kernels have that shape
                                  (12 with 4 realizations, 16 with 2)                    */
     int32_t split;            /* N_t-splits per frequency block: 0 = auto (chunks of
-                                 64 .. 65,536 samples), else 1 .. 65535                 */
+                                 64 .. 16,384 samples), else 1 .. 65535                 */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */
     int32_t batch_rhs;        /* lsp_batch with n_real > 1: realizations sharing one pass
@@ -214,7 +214,7 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  * exactly as the one-at-a-time kernel with the same strip length would.
  * A work item sums over all samples of its curve in FP32 (the batch does not
  * split N_t), so curves far beyond 10^6 samples are better served by
- * lsp_periodogram, which bounds each running sum to 65,536 samples.
+ * lsp_periodogram, which bounds each running sum to 16,384 samples.
  * At least one output must be given.  Arrays may be host or device pointers
  * (metadata is read on the host in either case); the sin/cos mode and strip
  * length follow the context's options (the naive FP32 phase is not offered).

@@ -87,9 +87,11 @@ constexpr int kMinChunk = 64;
 // Most samples per N_t chunk that the launch-shape heuristic makes.  Each
 // thread's FP32 running sums cover one chunk (the paper's chunked summation,
 // Sec. 4.2, at a coarser grain) and the chunks are merged with compensated
-// sums, so the rounding error of a sum stays near that of 65,536 terms
-// however large N_t grows.
-constexpr int64_t kMaxChunk = int64_t(1) << 16;
+// sums, so the rounding error of a sum stays near that of 16,384 terms
+// however large N_t grows (on the 382,003 x 1,528,064 paper shape, chunks of
+// 16k instead of 64k samples took the largest |dP| from 9e-6 to 1e-6 of max P,
+// at no cost in time).
+constexpr int64_t kMaxChunk = int64_t(1) << 14;
 
 // Frequencies covered by one CTA of the main kernel.
 inline int freqs_per_block(int F) { return kMainThreads * F; }

@@ -382,7 +382,7 @@ def test_largest_accepted_grid(ctx, kind):
 @pytest.mark.parametrize("kind", ["classic", "floating_mean"])
 def test_long_curve_chunks_bound_the_fp32_sums(ctx, kind):
     """2^25 samples (88x the paper's longest curve) on a short grid around an
-    injected line: the launch splits N_t into chunks of at most 65,536 samples
+    injected line: the launch splits N_t into chunks of at most 16,384 samples
     whose FP32 running sums are merged with compensated sums, so the peak
     keeps its 1e-4 relative bound against the FP64 oracle."""
     rng = np.random.default_rng(25)
