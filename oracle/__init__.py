@@ -18,8 +18,8 @@ arrays.  Every routine cites the passage of the paper it follows:
 * ``gls_at`` / ``gls_lsq`` -- floating-mean weighted periodogram (Sec. 6.3) and its
   brute-force least-squares reading
 * ``philox4x32_10`` / ``noise`` -- counter-based Gaussian noise for Sec. 6.2's
-  Monte-Carlo use (Salmon et al. 2011; Box & Muller 1958); parity unpinned
-  against the published known-answer vectors (statistical pins only)
+  Monte-Carlo use (Salmon et al. 2011; Box & Muller 1958); the generator is
+  pinned against the authors' published known-answer vectors
 
 Parity status of each routine is listed in ``tests/test_oracle_pins.py``.
 """

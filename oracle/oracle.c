@@ -382,10 +382,9 @@ int oracle_window_at(const double *t, int64_t n, const double *freqs, int64_t nf
  * Philox-4x32-10 (Salmon, Moraes, Dror & Shaw 2011, "Parallel random
  * numbers: as easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies and
  * a Feistel-like swap, with a Weyl-sequence key schedule between rounds.
- * Parity unpinned against the published known-answer vectors (not reproduced
- * here): only statistical pins hold it, and the GPU generator is compared
- * with this one.  What the Monte-Carlo results depend on -- independent
- * N(0,1) draws -- is pinned downstream by exact Beta and Dirichlet laws.
+ * Pinned word for word against the authors' published known-answer vectors
+ * (tests/golden/philox4x32_10_kat.txt); the GPU generator is compared with
+ * this one bit for bit.
  */
 void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
 {
@@ -528,7 +527,8 @@ int oracle_gls_at(const double *t, const double *X, const double *dy, int64_t n,
  * closed form above: the weighted least-squares fit of the data by the span of
  * {1, cos wt, sin wt}, found by modified Gram-Schmidt (two sweeps) in the
  * weighted inner product, in long double; a basis vector whose remainder has
- * weighted length below 2^-30 adds nothing (rank-deficient frequencies).
+ * squared weighted length at most 2^-60 (length at most 2^-30) adds nothing
+ * (rank-deficient frequencies).
  * P = (N_t/2) (1 - chi2_fit / chi2_offset).  Tiny n only.
  */
 int oracle_gls_lsq(const double *t, const double *X, const double *dy, int64_t n, double f, double *P)

@@ -15,7 +15,10 @@ Parity status per oracle routine:
   grid ................. pinned (Eq. 10-11 arithmetic on the paper's configurations)
   periodogram_fp32phase_at pinned (equals exact form at small f*t; float rounding model)
   window_at ............ pinned (Dirichlet-kernel closed form)
-  philox4x32_10 / noise  pinned statistically (bit balance, avalanche, normality)
+  philox4x32_10 ........ pinned (the authors' published known-answer vectors,
+                         tests/golden/philox4x32_10_kat.txt; bit balance, avalanche)
+  noise ................ pinned (Box-Muller of pinned Philox words: normality, stream
+                         separation, exact Dirichlet law of even-grid noise maxima)
 """
 import os
 
@@ -211,6 +214,26 @@ def test_fp32_phase_model():
     exact = oracle.periodogram(t, X, df, df, k0 + 4)[ks]
     approx = oracle.periodogram_fp32phase_at(t, X, df, df, ks)
     assert np.max(np.abs(exact - approx)) > 3e-4 * exact.max()
+
+
+def _philox_kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                assert len(w) == 10
+                rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    # Salmon et al. 2011: the published Philox-4x32-10 known answers, word for word.
+    rows = _philox_kat_rows()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = oracle.philox4x32_10(ctr, key)
+        assert [int(x) for x in got] == want, (["%08x" % x for x in got], ["%08x" % x for x in want])
 
 
 def test_philox_bits_and_avalanche():
