@@ -118,9 +118,13 @@ lsp_status lsp_set_stream(lsp_ctx *ctx, void *cuda_stream);
  * paper's grid is f_0 = df, see lsp_grid).  P_out[N_f]: FP32 output.
  * N_t >= 2, 0 <= N_f < 2^31.  N_f = 0 is a no-op.  A term of Eq. 1 whose
  * denominator falls below N_t * 2^-16 (e.g. the sine term at the Nyquist
- * frequency of an even grid) is taken as zero.
- * Errors: INVALID_ARG, NONFINITE (f_0/df at call time; t/X on the device),
- * DEGENERATE (zero variance, on the device), OOM, CUDA.
+ * frequency of an even grid) is taken as zero.  The fixed-point phase needs
+ * |t_j - t_min| f_0 and |t_j - t_min| df below 2^52 turns; beyond that the
+ * call's P is NaN and lsp_sync returns INVALID_ARG.
+ * Errors: INVALID_ARG (also the phase range, on the device), NONFINITE
+ * (f_0/df at call time; t/X on the device), DEGENERATE (zero variance, on
+ * the device), OOM, CUDA.  Every entry point that takes arrays refuses, with
+ * INVALID_ARG, device memory that belongs to another GPU than the context's.
  */
 lsp_status lsp_periodogram(lsp_ctx *ctx, const double *t, const double *X, int64_t N_t,
                            double f_0, double df, int64_t N_f, float *P_out);
@@ -361,6 +365,73 @@ lsp_status lsp_fap_train_step(lsp_ctx *ctx, int32_t B, const int32_t *rows, int3
                               const float *features, const float *counts, const float *targets,
                               float lr, float *loss_out);
 
+/* Report of lsp_fap_train (host struct, filled on success). */
+typedef struct lsp_train_report {
+    int32_t best_step;        /* steps taken before the kept weights (0: the network as it
+                                 was before the call)                                    */
+    int32_t evaluations;      /* validation passes run, the one before training included  */
+    float val_loss_initial;   /* validation pinball loss before the first step (right after
+                                 lsp_fap_init: exactly Eq. 3's quantiles)                 */
+    float val_loss_best;      /* validation pinball loss of the kept weights              */
+    float train_loss_last;    /* mean minibatch pinball loss of the steps after the
+                                 second-to-last validation pass                           */
+    float gpu_ms;             /* CUDA-event time of the whole loop on the context's stream */
+} lsp_train_report;
+
+/*
+ * Training set, validation set and schedule of lsp_fap_train.  Every table is
+ * a device array of the context's GPU (FP32, row-major).
+ */
+typedef struct lsp_train_opts {
+    int32_t n_pat;              /* training patterns (>= 1)                                   */
+    int32_t n_rows;             /* training rows (>= 1): row r pairs pattern r % n_pat with
+                                   target r (several noise realizations per pattern)         */
+    const float *features;      /* [n_pat][32]: lsp_fap_features of the patterns            */
+    const float *counts;        /* [n_pat][2]: (N_t, N_f) of the patterns                   */
+    const float *targets;       /* [n_rows]: the largest P of row r's noise periodogram      */
+    int32_t n_val_pat;          /* validation patterns (1 .. 65535)                          */
+    int32_t n_val_real;         /* noise realizations per validation pattern (>= 1)          */
+    const float *val_features;  /* [n_val_pat][32]                                           */
+    const float *val_counts;    /* [n_val_pat][2]                                            */
+    const float *val_targets;   /* [n_val_real][n_val_pat]: largest P of realization r of
+                                   validation pattern i at [r][i]                            */
+    int32_t steps;              /* Adam steps (>= 1)                                          */
+    int32_t batch;              /* rows per minibatch (1 .. 65536), drawn with replacement   */
+    int32_t warmup_steps;       /* linear warm-up of the learning rate (0 .. steps)          */
+    int32_t eval_every;         /* validation pass every so many steps, and after the last
+                                   (0: only before the first and after the last step)       */
+    float lr;                   /* peak learning rate (> 0)                                  */
+    float lr_final;             /* cosine decay ends at lr * lr_final (0 .. 1)               */
+    float weight_decay;         /* decoupled weight decay per unit of lr (>= 0; 0 = Adam)   */
+    int32_t reserved0;          /* must be zero                                              */
+    uint64_t seed;              /* minibatch draws: Philox-4x32-10 block (i/4, step,
+                                   0x54524e52, 0) under key (seed low, seed high), word i%4
+                                   w gives row floor(w n_rows / 2^32)                       */
+    float *val_history;         /* optional [evaluations]: validation loss of each pass,
+                                   host or device (size: 2 + (steps - 1) / eval_every with
+                                   eval_every > 0, else 2)                                   */
+    float *train_history;       /* optional, same size: mean minibatch loss of the steps
+                                   before each pass (NaN for the pass before training)      */
+    lsp_train_report *report;   /* optional host struct                                      */
+} lsp_train_opts;
+
+/*
+ * Train the surrogate's network (lsp_fap_init or lsp_fap_load first) for
+ * opt->steps Adam steps entirely on the GPU: each step draws its minibatch
+ * rows from the Philox stream above, runs the forward and backward pass and
+ * the Adam update (beta 0.9/0.999, eps 1e-8, decoupled weight decay) at the
+ * step's learning rate (linear warm-up, then cosine decay from lr to
+ * lr * lr_final); every eval_every steps the mean pinball loss of the
+ * validation set is reduced on the device, and the weights with the lowest
+ * validation loss so far (the initial weights included) are kept; they are
+ * the context's network when the call returns.  This is the Monte-Carlo
+ * estimate Sec. 6.2 asks for, learned: the targets are noise-periodogram
+ * maxima from lsp_batch, and the head starts from Eq. 3's quantiles.
+ * Blocks until the loop is done.  Deterministic for a given seed.
+ * Errors: INVALID_ARG (sizes, schedule, non-device tables), NO_MODEL, OOM, CUDA.
+ */
+lsp_status lsp_fap_train(lsp_ctx *ctx, const lsp_train_opts *opt);
+
 /* Gradient of the mean pinball loss of B rows w.r.t. the flat parameter
  * vector (layout W1[32][H] b1 W2[H][H] b2 W3[H][H] b3 W4[H][9] b4) into
  * grad_out, without updating anything; loss_out as above. */
@@ -400,16 +471,23 @@ void lsp_destroy(lsp_ctx *ctx);
  * Scratch: one file-scope device array of 64 MiB + 8 KiB that every GPU which
  * loads the library holds until the process exits.  Limit: 2 <= N_t <= 524,288
  * (larger N_t returns LSP_ERR_INVALID_ARG); N_f < 2^31 as for lsp_periodogram.
- * t, X and P_out must be device pointers on the current device (else
- * INVALID_ARG); the work is queued on `cuda_stream` (NULL: the legacy default
- * stream) and the call returns without waiting.  The first call on a device,
+ * Accuracy is that of lsp_periodogram: every FP32 running sum covers at most
+ * 16,384 samples.  When the partial sums of that many chunks do not fit the
+ * array at once (N_t > 16,384 with a long grid: at N_t = 524,288, beyond
+ * 98,304 frequencies), the grid is evaluated in frequency tiles, one
+ * main-kernel launch each, with the phase origin of each tile moved exactly.
+ * t, X and P_out must be device (or managed) memory of the current device:
+ * host memory and device memory of another GPU return INVALID_ARG.  The work
+ * is queued on `cuda_stream` (NULL: the legacy default stream) and the call
+ * returns without waiting.  The first call on a device,
  * with that device current, looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any
  * stream capture.  Every call shares the one array and it keeps the last
  * call's contents, so calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialized by the caller.  Data errors
- * found on the device (non-finite input, zero variance) are not reported by
- * status: they show as NaN in P_out.
+ * found on the device (non-finite input, zero variance, a phase beyond the
+ * 2^52-turn range of the fixed-point phase) are not reported by status: they
+ * show as NaN in P_out.
  * Errors: INVALID_ARG, NONFINITE (f_0/df), CUDA.
  */
 lsp_status lsp_periodogram_noalloc(const double *t, const double *X, int64_t N_t, double f_0,

@@ -31,7 +31,8 @@ def _nvcc():
 
 
 def _deps_mtime():
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+             + glob.glob(os.path.join(INCLUDE, "*.h")))
     return max((os.path.getmtime(f) for f in files), default=0.0)
 
 

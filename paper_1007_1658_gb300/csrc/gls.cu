@@ -171,7 +171,8 @@ __device__ __forceinline__ float gls_value(double XC, double XS, double C, doubl
     double p = 0.0;
     if (den1 > thr) p += num1 / den1;
     if (den2 > thr) p += num2 / den2;
-    return (float)(0.5 * n * p);
+    const double probe = z2 + R + T;  // NaN sums give NaN, not the 0 of the clamps above
+    return probe == probe ? (float)(0.5 * n * p) : (float)probe;
 }
 
 template <int F, int MODE>

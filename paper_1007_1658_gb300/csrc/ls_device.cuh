@@ -101,7 +101,9 @@ __device__ __forceinline__ void merge_chunks(const float* __restrict__ part, int
 // cos 2wtau = A/R, sin 2wtau = B/R, and the two denominators of Eq. 5 are
 // (N + R)/2 and (N - R)/2; the two numerators are (|Z|^2 +- Re(e^{-2iwtau} Z^2))/2
 // with Z = XC + i XS.  No trig, and R = 0 (tau undefined) takes wtau = 0.
-// A term whose denominator is below N 2^-16 is taken as zero.
+// A term whose denominator is below N 2^-16 is taken as zero.  A NaN among
+// the sums (non-finite data, or data the prep kernels refused) gives NaN: the
+// clamps and threshold tests below would otherwise turn it into 0.
 __device__ __forceinline__ float periodogram_value(float XC, float XS, float CC, float CS, float n) {
     const float A = 2.f * CC - n;
     const float B = 2.f * CS;
@@ -121,7 +123,8 @@ __device__ __forceinline__ float periodogram_value(float XC, float XS, float CC,
     float P = 0.f;
     if (den1 > thr) P += num1 / den1;
     if (den2 > thr) P += num2 / den2;
-    return 0.5f * P;
+    const float probe = z2 + R;
+    return probe == probe ? 0.5f * P : probe;
 }
 
 // The four running sums of Eq. 8 for a strip of F adjacent frequencies

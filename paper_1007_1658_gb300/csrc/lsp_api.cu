@@ -10,6 +10,7 @@
 #include <thread>
 
 #include "lsp_ctx.h"
+#include "lsp_testing.h"
 
 using lsp::CurveStats;
 using lsp::MainShape;
@@ -221,9 +222,12 @@ lsp_status lsp_periodogram(lsp_ctx* ctx, const double* t, const double* X, int64
     DeviceGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
 
-    const bool t_dev = is_device_ptr(t), x_dev = is_device_ptr(X), p_dev = is_device_ptr(P_out);
-    const MainShape s = choose_shape(ctx, N_t, N_f);
     lsp_status rs;
+    bool t_dev = false, x_dev = false, p_dev = false;
+    if ((rs = where(ctx, t, &t_dev)) != LSP_OK || (rs = where(ctx, X, &x_dev)) != LSP_OK ||
+        (rs = where(ctx, P_out, &p_dev)) != LSP_OK)
+        return rs;
+    const MainShape s = choose_shape(ctx, N_t, N_f);
     if ((rs = ensure(ctx, ctx->recA, (size_t)N_t * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->recB, (size_t)N_t * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->stats, sizeof(CurveStats))) != LSP_OK) return rs;
@@ -251,17 +255,25 @@ lsp_status lsp_periodogram(lsp_ctx* ctx, const double* t, const double* X, int64
     const bool timing = ctx->opt.timing != 0;
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     CurveStats* stats = (CurveStats*)ctx->stats.p;
-    LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d,
-                                         (lsp::StatPart*)ctx->stat_parts.p, (unsigned*)ctx->stat_counters.p, st));
-    LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
-                                           (uint4*)ctx->recA.p, (float4*)ctx->recB.p,
-                                           s.mode == lsp::kModeNaive ? (float2*)ctx->recN.p : nullptr, nullptr, st));
+    {
+        NvtxRange r("lsp_periodogram.prep");
+        LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d,
+                                             (lsp::StatPart*)ctx->stat_parts.p, (unsigned*)ctx->stat_counters.p, st));
+        LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
+                                               (uint4*)ctx->recA.p, (float4*)ctx->recB.p,
+                                               s.mode == lsp::kModeNaive ? (float2*)ctx->recN.p : nullptr, nullptr,
+                                               st, nullptr, nullptr, ctx->status_d));
+    }
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
-    LSP_CUDA(ctx, lsp::launch_main(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
-                                   (const float2*)ctx->recN.p, N_t, N_f, f_0, df, (float*)ctx->part.p, pd, st));
+    {
+        NvtxRange r("lsp_periodogram.main");
+        LSP_CUDA(ctx, lsp::launch_main(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
+                                       (const float2*)ctx->recN.p, N_t, N_f, f_0, df, (float*)ctx->part.p, pd, st));
+    }
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
     ctx->last_launches = 3;
     if (s.split > 1) {
+        NvtxRange r("lsp_periodogram.finalize");
         LSP_CUDA(ctx, lsp::launch_finalize(s, (const float*)ctx->part.p, N_t, N_f, pd, st));
         ctx->last_launches = 4;
     }
@@ -299,6 +311,9 @@ lsp_status lsp_sync(lsp_ctx* ctx, double timeout_s) {
         LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (flags & lsp::kStatusNonFinite) return fail(ctx, LSP_ERR_NONFINITE, "non-finite value in t or X");
         if (flags & lsp::kStatusBadWeight) return fail(ctx, LSP_ERR_INVALID_ARG, "dy must be finite and > 0");
+        if (flags & lsp::kStatusPhaseRange)
+            return fail(ctx, LSP_ERR_INVALID_ARG,
+                        "(t - t_min) f_0 or (t - t_min) df reaches 2^52 turns: beyond the exact fixed-point phase");
         return fail(ctx, LSP_ERR_DEGENERATE, "X has zero variance");
     }
     return LSP_OK;
@@ -320,6 +335,16 @@ lsp_status lsp_last_timing(lsp_ctx* ctx, float* ms_prep, float* ms_main, float* 
 
 int32_t lsp_last_launch_count(const lsp_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
 
+int32_t lsp_test_pointer_kind(int32_t memory_type, int32_t pointer_device, int32_t device) {
+    return pointer_kind(memory_type, pointer_device, device);
+}
+
+lsp_status lsp_test_fail_allocation(lsp_ctx* ctx, int32_t n) {
+    if (!ctx || n < 0) return LSP_ERR_INVALID_ARG;
+    ctx->fail_alloc_in = n;
+    return LSP_OK;
+}
+
 const char* lsp_last_error(const lsp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 void lsp_destroy(lsp_ctx* ctx) {
@@ -334,6 +359,12 @@ void lsp_destroy(lsp_ctx* ctx) {
                       &ctx->b_seed,  &ctx->b_off,  &ctx->b_nf,   &ctx->b_f0,    &ctx->b_df,   &ctx->b_poff,
                       &ctx->b_t,     &ctx->b_X,    &ctx->b_P,    &ctx->b_maxP,  &ctx->b_argmax};
     for (DevBuf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    lsp::host::FapState& f = ctx->fap;
+    DevBuf* fbufs[] = {&f.params, &f.grad, &f.m,    &f.v,    &f.mu_sig, &f.ws,    &f.act,  &f.X,
+                       &f.cnt,    &f.y,    &f.loss, &f.q,    &f.rows,   &f.W,     &f.W_off, &f.nw,
+                       &f.counts, &f.best, &f.train_state, &f.hist};
+    for (DevBuf* b : fbufs)
         if (b->p) cudaFree(b->p);
     if (ctx->status_d) cudaFree(ctx->status_d);
     if (ctx->status_h) cudaFreeHost(ctx->status_h);

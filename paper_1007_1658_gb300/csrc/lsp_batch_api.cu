@@ -94,9 +94,10 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
     if (P_out && (rs = device_view(ctx, P_off, (size_t)n_curves + 1, ctx->b_poff, &d_poff)) != LSP_OK) return rs;
     if ((rs = device_view(ctx, t, (size_t)total, ctx->b_t, &d_t)) != LSP_OK) return rs;
     if (!noise && (rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
-    const bool p_dev = !P_out || is_device_ptr(P_out);
-    const bool m_dev = !maxP_out || is_device_ptr(maxP_out);
-    const bool a_dev = !argmax_out || is_device_ptr(argmax_out);
+    bool p_dev = true, m_dev = true, a_dev = true;
+    if (P_out && (rs = where(ctx, P_out, &p_dev)) != LSP_OK) return rs;
+    if (maxP_out && (rs = where(ctx, maxP_out, &m_dev)) != LSP_OK) return rs;
+    if (argmax_out && (rs = where(ctx, argmax_out, &a_dev)) != LSP_OK) return rs;
     const size_t n_out = (size_t)n_real * (size_t)n_curves;
 
     // ---- workspace (all allocations happen before any capture) ----
@@ -123,6 +124,7 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
                       pl.F == F && pl.R == R && pl.noise == noise && pl.ptrs == ptrs && pl.t_off == off &&
                       pl.nf == nf && pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
     if (!same) {
+        NvtxRange r("lsp_batch.plan");
         drop_plan(ctx);
         // work list: curves longest first (each item costs ~N_t), then blocks, then realizations;
         // with single-realization strips longer than the tail strip, the frequencies after a
@@ -179,7 +181,7 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
             e = lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0,
                                          (const lsp::CurveStats*)ctx->b_stats.p, (uint4*)ctx->b_recA.p,
                                          (float4*)ctx->b_recB.p, nullptr, noise ? nullptr : (float*)ctx->b_xr.p,
-                                         cst);
+                                         cst, nullptr, nullptr, ctx->status_d);
         }
         if (e == cudaSuccess && noise)
             e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
@@ -235,7 +237,10 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     }
-    LSP_CUDA(ctx, cudaGraphLaunch(pl.exec, st));
+    {
+        NvtxRange r("lsp_batch.launch");
+        LSP_CUDA(ctx, cudaGraphLaunch(pl.exec, st));
+    }
     if (timing) {
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[3], st));
@@ -267,10 +272,12 @@ lsp_status lsp_noise(lsp_ctx* ctx, uint64_t seed, int32_t curve, int32_t real, i
     if (N == 0) return LSP_OK;
     if (N > (int64_t(1) << 34)) return fail(ctx, LSP_ERR_INVALID_ARG, "N too large");
     DeviceGuard guard(ctx->device);
-    const bool dev = is_device_ptr(out);
+    bool dev = false;
+    lsp_status rs = where(ctx, out, &dev);
+    if (rs != LSP_OK) return rs;
     float* d = out;
     if (!dev) {
-        lsp_status rs = ensure(ctx, ctx->p_stage, (size_t)N * 4);
+        rs = ensure(ctx, ctx->p_stage, (size_t)N * 4);
         if (rs != LSP_OK) return rs;
         d = (float*)ctx->p_stage.p;
     }

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lsp.h"
 #include "lsp_kernels.cuh"
 
@@ -48,6 +50,7 @@ struct FapState {
     int64_t n_params = 0;
     int64_t step = 0;
     DevBuf params, grad, m, v, mu_sig, ws, act, X, cnt, y, loss, q, rows, W, W_off, nw, counts;
+    DevBuf best, train_state, hist;  // lsp_fap_train: kept weights, loop scalars, histories
 };
 
 }  // namespace host
@@ -80,10 +83,22 @@ struct lsp_ctx {
     bool timing_valid = false;
     bool has_finalize = false;
     int last_launches = 0;
+    int fail_alloc_in = 0;  // test hook: the n-th workspace allocation from now fails (0: never)
 };
 
 namespace lsp {
 namespace host {
+
+// An NVTX range named for a stage of a call (prep, main, finalize, batch),
+// open for the scope of the host code that enqueues it, so that a profiler's
+// timeline can tie kernels to the library's stages.  Costs a few nanoseconds
+// when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Makes the context's device current for the scope of a call and restores the
 // caller's device afterwards.
@@ -135,6 +150,8 @@ inline lsp_status ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
         b.cap = 0;
     }
     size_t want = bytes + bytes / 4 + 256;
+    if (ctx->fail_alloc_in > 0 && --ctx->fail_alloc_in == 0)
+        return fail(ctx, LSP_ERR_OOM, "cudaMalloc(workspace): allocation failure injected by lsp_test_fail_allocation");
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -155,13 +172,38 @@ inline lsp_status ensure_zeroed(lsp_ctx* ctx, DevBuf& b, size_t bytes) {
     return LSP_OK;
 }
 
-inline bool is_device_ptr(const void* p) {
+// Where a caller's array lives, decided from its CUDA pointer attributes
+// (memory type and owning device): host memory (pageable, registered or
+// pinned; staged through copies), device memory of the context's GPU or
+// managed memory (used in place), or device memory of another GPU, which the
+// library refuses: a kernel would reach it only through a peer mapping the
+// caller never asked for, or fault.
+enum PtrKind : int { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+
+inline int pointer_kind(int memory_type, int pointer_device, int device) {
+    if (memory_type == cudaMemoryTypeManaged) return kPtrDevice;
+    if (memory_type == cudaMemoryTypeDevice) return pointer_device == device ? kPtrDevice : kPtrOtherDevice;
+    return kPtrHost;
+}
+
+inline int pointer_kind_of(const void* p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return kPtrHost;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return pointer_kind((int)a.type, a.device, device);
+}
+
+// *on_dev: the array is on the context's GPU (true) or on the host (false);
+// INVALID_ARG for an array on another GPU.
+inline lsp_status where(lsp_ctx* ctx, const void* p, bool* on_dev) {
+    const int k = pointer_kind_of(p, ctx->device);
+    if (k == kPtrOtherDevice)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "an array argument is device memory of another GPU (context on device %d)",
+                    ctx->device);
+    *on_dev = k == kPtrDevice;
+    return LSP_OK;
 }
 
 // Copy n elements of a host or device array into a host vector (ordered on
@@ -170,7 +212,10 @@ template <class T>
 inline lsp_status fetch(lsp_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
     dst.resize(n);
     if (n == 0) return LSP_OK;
-    if (is_device_ptr(src)) {
+    bool dev = false;
+    lsp_status ws = where(ctx, src, &dev);
+    if (ws != LSP_OK) return ws;
+    if (dev) {
         LSP_CUDA(ctx, cudaMemcpyAsync(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
         LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     } else {
@@ -197,7 +242,10 @@ inline lsp_status ensure_pinned(lsp_ctx* ctx, size_t bytes) {
 // else a context buffer filled from it (asynchronously, outside the graph).
 template <class T>
 inline lsp_status device_view(lsp_ctx* ctx, const T* src, size_t n, DevBuf& buf, const T** out) {
-    if (is_device_ptr(src)) {
+    bool dev = false;
+    lsp_status ws = where(ctx, src, &dev);
+    if (ws != LSP_OK) return ws;
+    if (dev) {
         *out = src;
         return LSP_OK;
     }

@@ -24,7 +24,10 @@ lsp_status need_model(lsp_ctx* ctx) {
 // Output staging: device pointer as is, else a context buffer copied back later.
 template <class T>
 lsp_status out_view(lsp_ctx* ctx, T* dst, size_t n, DevBuf& buf, T** d, bool* host) {
-    *host = !is_device_ptr(dst);
+    bool dev = false;
+    lsp_status ws = where(ctx, dst, &dev);
+    if (ws != LSP_OK) return ws;
+    *host = !dev;
     if (!*host) {
         *d = dst;
         return LSP_OK;
@@ -91,7 +94,10 @@ lsp_status fap_run(lsp_ctx* ctx, int B, const int32_t* rows, int n_pat, const fl
 
 lsp_status copy_loss(lsp_ctx* ctx, float* loss_out) {
     if (!loss_out) return LSP_OK;
-    if (is_device_ptr(loss_out)) {
+    bool dev = false;
+    lsp_status ws = where(ctx, loss_out, &dev);
+    if (ws != LSP_OK) return ws;
+    if (dev) {
         LSP_CUDA(ctx, cudaMemcpyAsync(loss_out, ctx->fap.loss.p, 4, cudaMemcpyDeviceToDevice, ctx->stream));
         return LSP_OK;
     }
@@ -180,7 +186,8 @@ lsp_status lsp_fap_features(lsp_ctx* ctx, int32_t n, const int64_t* t_off, const
                                          nullptr, nullptr, st));
     LSP_CUDA(ctx, lsp::launch_prep_records(d_t, nullptr, d_off, 0, n, max_n, d_df, d_df, 0.0, 0.0,
                                            (const lsp::CurveStats*)ctx->b_stats.p, (uint4*)ctx->b_recA.p,
-                                           (float4*)ctx->b_recB.p, nullptr, nullptr, st));
+                                           (float4*)ctx->b_recB.p, nullptr, nullptr, st, nullptr, nullptr,
+                                           ctx->status_d));
     if (!items.empty()) {
         const int grid = (int)std::min<int64_t>((int64_t)lsp::window_occupancy(F) * ctx->sms, (int64_t)items.size());
         LSP_CUDA(ctx, lsp::launch_window(F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
@@ -228,8 +235,13 @@ lsp_status lsp_fap_train_step(lsp_ctx* ctx, int32_t B, const int32_t* rows, int3
     if (rs != LSP_OK) return rs;
     if (B < 1 || n_pat < 1 || !rows || !features || !counts || !targets || !(lr > 0.f))
         return fail(ctx, LSP_ERR_INVALID_ARG, "bad training-step argument");
-    if (!is_device_ptr(rows) || !is_device_ptr(features) || !is_device_ptr(counts) || !is_device_ptr(targets))
-        return fail(ctx, LSP_ERR_INVALID_ARG, "training tables must be device arrays");
+    {
+        bool d0 = false, d1 = false, d2 = false, d3 = false;
+        if ((rs = where(ctx, rows, &d0)) != LSP_OK || (rs = where(ctx, features, &d1)) != LSP_OK ||
+            (rs = where(ctx, counts, &d2)) != LSP_OK || (rs = where(ctx, targets, &d3)) != LSP_OK)
+            return rs;
+        if (!d0 || !d1 || !d2 || !d3) return fail(ctx, LSP_ERR_INVALID_ARG, "training tables must be device arrays");
+    }
     DeviceGuard guard(ctx->device);
     FapState& f = ctx->fap;
     if ((rs = fap_run(ctx, B, rows, n_pat, features, counts, targets, true, nullptr)) != LSP_OK) return rs;
@@ -237,8 +249,118 @@ lsp_status lsp_fap_train_step(lsp_ctx* ctx, int32_t B, const int32_t* rows, int3
     const double b1 = 0.9, b2 = 0.999;
     const float c1 = (float)(1.0 - std::pow(b1, (double)f.step)), c2 = (float)(1.0 - std::pow(b2, (double)f.step));
     LSP_CUDA(ctx, lsp::mlp_adam(f.n_params, (float*)f.params.p, (const float*)f.grad.p, (float*)f.m.p,
-                                (float*)f.v.p, lr, (float)b1, (float)b2, c1, c2, 1e-8f, ctx->stream));
+                                (float*)f.v.p, lr, (float)b1, (float)b2, c1, c2, 1e-8f, 0.f, ctx->stream));
     return copy_loss(ctx, loss_out);
+}
+
+lsp_status lsp_fap_train(lsp_ctx* ctx, const lsp_train_opts* o) {
+    if (!ctx) return LSP_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (!o) return fail(ctx, LSP_ERR_INVALID_ARG, "null options");
+    lsp_status rs = need_model(ctx);
+    if (rs != LSP_OK) return rs;
+    if (o->n_pat < 1 || o->n_rows < 1 || o->n_val_pat < 1 || o->n_val_pat > 65535 || o->n_val_real < 1 ||
+        (int64_t)o->n_val_pat * o->n_val_real > (int64_t(1) << 31))
+        return fail(ctx, LSP_ERR_INVALID_ARG, "training or validation set size out of range");
+    if (o->steps < 1 || o->batch < 1 || o->batch > 65536 || o->warmup_steps < 0 || o->warmup_steps > o->steps ||
+        o->eval_every < 0 || o->reserved0 != 0)
+        return fail(ctx, LSP_ERR_INVALID_ARG, "steps >= 1, batch in [1, 65536], warmup in [0, steps], eval_every >= 0");
+    if (!(o->lr > 0.f) || !std::isfinite(o->lr) || !(o->lr_final >= 0.f && o->lr_final <= 1.f) ||
+        !(o->weight_decay >= 0.f) || !std::isfinite(o->weight_decay))
+        return fail(ctx, LSP_ERR_INVALID_ARG, "lr > 0, lr_final in [0, 1], weight_decay >= 0");
+    const void* tables[] = {o->features, o->counts, o->targets, o->val_features, o->val_counts, o->val_targets};
+    for (const void* p : tables) {
+        bool dev = false;
+        if (!p) return fail(ctx, LSP_ERR_INVALID_ARG, "null training table");
+        if ((rs = where(ctx, p, &dev)) != LSP_OK) return rs;
+        if (!dev) return fail(ctx, LSP_ERR_INVALID_ARG, "training tables must be device arrays");
+    }
+    bool vh_dev = false, th_dev = false;
+    if (o->val_history && (rs = where(ctx, o->val_history, &vh_dev)) != LSP_OK) return rs;
+    if (o->train_history && (rs = where(ctx, o->train_history, &th_dev)) != LSP_OK) return rs;
+    DeviceGuard guard(ctx->device);
+    FapState& f = ctx->fap;
+    cudaStream_t st = ctx->stream;
+    const int B = o->batch, V = o->n_val_pat;
+    const int passes = o->eval_every > 0 ? 2 + (o->steps - 1) / o->eval_every : 2;
+    if ((rs = fap_batch_buffers(ctx, std::max(B, V))) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, f.rows, (size_t)B * 4)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, f.best, (size_t)f.n_params * 4)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, f.train_state, 64)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, f.hist, (size_t)passes * 2 * 4)) != LSP_OK) return rs;
+    float* ts = (float*)f.train_state.p;  // {val, best loss, best step, acc sum, acc count, flag}
+    float* val = ts;
+    float* state = ts + 1;
+    float* acc = ts + 3;
+    int* flag = (int*)(ts + 5);
+    float* vhist = (float*)f.hist.p;
+    float* thist = vhist + passes;
+    LSP_CUDA(ctx, cudaMemsetAsync(ts, 0, 64, st));
+    LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
+    int e = 0;
+    auto validate = [&](int step) -> lsp_status {
+        float* q = nullptr;
+        lsp_status r = fap_run(ctx, V, nullptr, V, o->val_features, o->val_counts, nullptr, false, &q);
+        if (r != LSP_OK) return r;
+        LSP_CUDA(ctx, lsp::train_pinball(q, o->val_targets, V, o->n_val_real, val, st));
+        LSP_CUDA(ctx, lsp::train_keep_best(val, state, step, flag, acc, vhist, thist, e, (const float*)f.params.p,
+                                           (float*)f.best.p, f.n_params, st));
+        ++e;
+        return LSP_OK;
+    };
+    if ((rs = validate(0)) != LSP_OK) return rs;
+    const double b1 = 0.9, b2 = 0.999, pi = 3.14159265358979323846;
+    for (int s = 0; s < o->steps; ++s) {
+        double lr;
+        if (s < o->warmup_steps) {
+            lr = (double)o->lr * (double)(s + 1) / (double)o->warmup_steps;
+        } else {
+            const double span = (double)std::max(1, o->steps - o->warmup_steps);
+            const double c = 0.5 * (1.0 + std::cos(pi * (double)(s - o->warmup_steps) / span));
+            lr = (double)o->lr * ((double)o->lr_final + (1.0 - (double)o->lr_final) * c);
+        }
+        LSP_CUDA(ctx, lsp::train_draw_rows(o->seed, (uint32_t)s, B, (uint32_t)o->n_rows, (int32_t*)f.rows.p, st));
+        if ((rs = fap_run(ctx, B, (const int32_t*)f.rows.p, o->n_pat, o->features, o->counts, o->targets, true,
+                          nullptr)) != LSP_OK)
+            return rs;
+        LSP_CUDA(ctx, lsp::train_accum_loss((const float*)f.loss.p, acc, st));
+        f.step += 1;
+        const float c1 = (float)(1.0 - std::pow(b1, (double)f.step));
+        const float c2 = (float)(1.0 - std::pow(b2, (double)f.step));
+        LSP_CUDA(ctx, lsp::mlp_adam(f.n_params, (float*)f.params.p, (const float*)f.grad.p, (float*)f.m.p,
+                                    (float*)f.v.p, (float)lr, (float)b1, (float)b2, c1, c2, 1e-8f, o->weight_decay,
+                                    st));
+        const bool last = s + 1 == o->steps;
+        if (last || (o->eval_every > 0 && (s + 1) % o->eval_every == 0))
+            if ((rs = validate(s + 1)) != LSP_OK) return rs;
+    }
+    // the kept weights become the network
+    LSP_CUDA(ctx, cudaMemcpyAsync(f.params.p, f.best.p, (size_t)f.n_params * 4, cudaMemcpyDeviceToDevice, st));
+    LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
+    float host_ts[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<float> hh((size_t)passes * 2);
+    LSP_CUDA(ctx, cudaMemcpyAsync(host_ts, ts, sizeof host_ts, cudaMemcpyDeviceToHost, st));
+    LSP_CUDA(ctx, cudaMemcpyAsync(hh.data(), vhist, hh.size() * 4, cudaMemcpyDeviceToHost, st));
+    if (o->val_history)
+        LSP_CUDA(ctx, cudaMemcpyAsync(o->val_history, vhist, (size_t)e * 4,
+                                      vh_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (o->train_history)
+        LSP_CUDA(ctx, cudaMemcpyAsync(o->train_history, thist, (size_t)e * 4,
+                                      th_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if ((rs = lsp_sync(ctx, -1.0)) != LSP_OK) return rs;
+    if (o->report) {
+        float ms = 0.f;
+        LSP_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        lsp_train_report& r = *o->report;
+        r.best_step = (int32_t)host_ts[2];
+        r.evaluations = e;
+        r.val_loss_initial = hh[0];
+        r.val_loss_best = host_ts[1];
+        r.train_loss_last = hh[(size_t)passes + (size_t)e - 1];
+        r.gpu_ms = ms;
+    }
+    ctx->timing_valid = false;
+    return LSP_OK;
 }
 
 lsp_status lsp_fap_gradients(lsp_ctx* ctx, int32_t B, const float* features, const float* counts,
@@ -255,7 +377,9 @@ lsp_status lsp_fap_gradients(lsp_ctx* ctx, int32_t B, const float* features, con
     if ((rs = device_view(ctx, counts, (size_t)B * 2, ctx->b_X, (const float**)&d_cnt)) != LSP_OK) return rs;
     if ((rs = device_view(ctx, targets, (size_t)B, ctx->b_xr, &d_y)) != LSP_OK) return rs;
     if ((rs = fap_run(ctx, B, nullptr, B, d_feat, d_cnt, d_y, true, nullptr)) != LSP_OK) return rs;
-    const cudaMemcpyKind k = is_device_ptr(grad_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    bool g_dev = false;
+    if ((rs = where(ctx, grad_out, &g_dev)) != LSP_OK) return rs;
+    const cudaMemcpyKind k = g_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     LSP_CUDA(ctx, cudaMemcpyAsync(grad_out, f.grad.p, (size_t)f.n_params * 4, k, ctx->stream));
     if (k == cudaMemcpyDeviceToHost) LSP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return copy_loss(ctx, loss_out);
@@ -273,7 +397,8 @@ lsp_status lsp_fap_eval(lsp_ctx* ctx, int32_t B, const float* features, const fl
     if ((rs = device_view(ctx, counts, (size_t)B * 2, ctx->b_X, (const float**)&d_cnt)) != LSP_OK) return rs;
     float* q = nullptr;
     if ((rs = fap_run(ctx, B, nullptr, B, d_feat, d_cnt, nullptr, false, &q)) != LSP_OK) return rs;
-    const bool dev = is_device_ptr(q_out);
+    bool dev = false;
+    if ((rs = where(ctx, q_out, &dev)) != LSP_OK) return rs;
     LSP_CUDA(ctx, cudaMemcpyAsync(q_out, q, (size_t)B * kNLev * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   ctx->stream));
     return dev ? LSP_OK : lsp_sync(ctx, -1.0);

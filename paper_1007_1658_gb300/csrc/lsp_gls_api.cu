@@ -59,8 +59,13 @@ lsp_status lsp_periodogram_gls(lsp_ctx* ctx, const double* t, const double* X, c
     DeviceGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
 
-    const bool t_dev = is_device_ptr(t), x_dev = is_device_ptr(X), p_dev = is_device_ptr(P_out);
-    const bool dy_dev = dy && is_device_ptr(dy);
+    bool t_dev = false, x_dev = false, p_dev = false, dy_dev = false;
+    {
+        lsp_status ws;
+        if ((ws = where(ctx, t, &t_dev)) != LSP_OK || (ws = where(ctx, X, &x_dev)) != LSP_OK ||
+            (ws = where(ctx, P_out, &p_dev)) != LSP_OK || (dy && (ws = where(ctx, dy, &dy_dev)) != LSP_OK))
+            return ws;
+    }
     const MainShape s = choose_gls_shape(ctx, N_t, N_f);
     lsp_status rs;
     if ((rs = ensure(ctx, ctx->recA, (size_t)N_t * 16)) != LSP_OK) return rs;
@@ -97,18 +102,25 @@ lsp_status lsp_periodogram_gls(lsp_ctx* ctx, const double* t, const double* X, c
     const bool timing = ctx->opt.timing != 0;
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     CurveStats* stats = (CurveStats*)ctx->stats.p;
-    LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d,
-                                         (lsp::StatPart*)ctx->stat_parts.p, (unsigned*)ctx->stat_counters.p, st,
-                                         dyd));
-    LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
-                                           (uint4*)ctx->recA.p, (float4*)ctx->recB.p, nullptr, nullptr, st, dyd,
-                                           (float*)ctx->recQ.p));
+    {
+        NvtxRange r("lsp_periodogram_gls.prep");
+        LSP_CUDA(ctx, lsp::launch_prep_stats(td, xd, nullptr, N_t, 1, stats, ctx->status_d,
+                                             (lsp::StatPart*)ctx->stat_parts.p, (unsigned*)ctx->stat_counters.p, st,
+                                             dyd));
+        LSP_CUDA(ctx, lsp::launch_prep_records(td, xd, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats,
+                                               (uint4*)ctx->recA.p, (float4*)ctx->recB.p, nullptr, nullptr, st, dyd,
+                                               (float*)ctx->recQ.p, ctx->status_d));
+    }
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
-    LSP_CUDA(ctx, lsp::launch_gls(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
-                                  (const float*)ctx->recQ.p, N_t, N_f, (float*)ctx->part.p, pd, st));
+    {
+        NvtxRange r("lsp_periodogram_gls.main");
+        LSP_CUDA(ctx, lsp::launch_gls(s, (const uint4*)ctx->recA.p, (const float4*)ctx->recB.p,
+                                      (const float*)ctx->recQ.p, N_t, N_f, (float*)ctx->part.p, pd, st));
+    }
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
     ctx->last_launches = 3;
     if (s.split > 1) {
+        NvtxRange r("lsp_periodogram_gls.finalize");
         LSP_CUDA(ctx, lsp::launch_gls_finalize(s, (const float*)ctx->part.p, N_t, N_f, pd, st));
         ctx->last_launches = 4;
     }
@@ -180,9 +192,10 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     if ((rs = device_view(ctx, t, (size_t)total, ctx->b_t, &d_t)) != LSP_OK) return rs;
     if ((rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
     if (dy && (rs = device_view(ctx, dy, (size_t)total, ctx->dy_stage, &d_dy)) != LSP_OK) return rs;
-    const bool p_dev = !P_out || is_device_ptr(P_out);
-    const bool m_dev = !maxP_out || is_device_ptr(maxP_out);
-    const bool a_dev = !argmax_out || is_device_ptr(argmax_out);
+    bool p_dev = true, m_dev = true, a_dev = true;
+    if (P_out && (rs = where(ctx, P_out, &p_dev)) != LSP_OK) return rs;
+    if (maxP_out && (rs = where(ctx, maxP_out, &m_dev)) != LSP_OK) return rs;
+    if (argmax_out && (rs = where(ctx, argmax_out, &a_dev)) != LSP_OK) return rs;
 
     // mode and strip length as for the single-curve floating-mean call
     const MainShape shape = choose_gls_shape(ctx, 1 << 20, 1 << 24);
@@ -230,10 +243,11 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     const int64_t max_n = off[order[0] + 1] - off[order[0]];
     LSP_CUDA(ctx, lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0, stats,
                                            (uint4*)ctx->b_recA.p, (float4*)ctx->b_recB.p, nullptr, nullptr, st,
-                                           d_dy, (float*)ctx->b_xr.p));
+                                           d_dy, (float*)ctx->b_xr.p, ctx->status_d));
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     int launches = 2;
     if (!items.empty()) {
+        NvtxRange r("lsp_batch_gls.main");
         const int occ = std::max(1, lsp::gls_batch_occupancy(mode, F));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
         LSP_CUDA(ctx, lsp::launch_gls_batch(mode, F, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),

@@ -12,6 +12,7 @@ enum : int {
     kStatusNonFinite = 1,
     kStatusDegenerate = 2,
     kStatusBadWeight = 4,   // a per-sample error that is not finite and > 0
+    kStatusPhaseRange = 8,  // |t - t_min| f_0 or |t - t_min| df reaches 2^52 turns
 };
 
 // Per-curve statistics written by prep_stats (Sec. 3 normalization, FP64).
@@ -57,11 +58,14 @@ cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* o
 // qout (floating-mean periodogram, stats from launch_prep_stats with the same
 // dy, or none for equal weights) receives q_j = sqrt(w_j), sum w = 1, and x_hat
 // becomes q_j (X_j - mean_w) / sd_w.
+// The fixed-point phases need |t_j - t_ref| f_0 and |t_j - t_ref| df below
+// 2^52 turns; a sample beyond that gets x_hat = NaN (so its periodogram is
+// NaN) and sets kStatusPhaseRange in *status when status is given.
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
                                 uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st,
-                                const double* dy = nullptr, float* qout = nullptr);
+                                const double* dy = nullptr, float* qout = nullptr, int* status = nullptr);
 
 // Kernel modes (how sin/cos and the phase are formed in the O(N_t N_f) loop).
 // kModeRecur3x2 is RECUR3 with the (cos, sin) pair carried through packed
@@ -205,7 +209,21 @@ size_t mlp_act_bytes(int H, int Bn, bool fp32);
 cudaError_t mlp_forward_backward(int H, int Bn, bool fp32, const float* params, const float* X, const float* cnt,
                                  const float* y, float* q, float* grad, float* loss, float* ws, void* act,
                                  cudaStream_t st);
+// Adam (Kingma & Ba 2015) with bias corrections c1, c2 and decoupled weight
+// decay wd (p -= lr wd p; 0 = plain Adam).
 cudaError_t mlp_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float c1,
-                     float c2, float eps, cudaStream_t st);
+                     float c2, float eps, float wd, cudaStream_t st);
+
+// ---- the training loop's device helpers (train.cu) ----
+// Minibatch rows of `step`, uniform over [0, n_rows), from a Philox stream.
+cudaError_t train_draw_rows(uint64_t seed, uint32_t step, int B, uint32_t n_rows, int32_t* rows, cudaStream_t st);
+// *out = mean pinball loss of q[n_pat][9] against y[n_real][n_pat] (fixed order).
+cudaError_t train_pinball(const float* q, const float* y, int n_pat, int n_real, float* out, cudaStream_t st);
+// acc = {sum, count} of the minibatch losses since the last validation pass.
+cudaError_t train_accum_loss(const float* loss, float* acc, cudaStream_t st);
+// Validation pass e after `step` steps: histories, and best = params when
+// *val beats state[0] = best loss (state[1] = its step).
+cudaError_t train_keep_best(const float* val, float* state, int step, int* flag, float* acc, float* val_hist,
+                            float* train_hist, int e, const float* params, float* best, int64_t n, cudaStream_t st);
 
 }  // namespace lsp

@@ -12,8 +12,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "lsp.h"
-#include "lsp_kernels.cuh"
+#include "lsp_ctx.h"
 
 namespace {
 
@@ -52,13 +51,22 @@ cudaError_t scratch_for(int dev, unsigned char** out, int* sms) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
+// Device memory of `dev` or managed memory; host memory and device memory of
+// another GPU are refused.
+bool on_device(const void* p, int dev) { return lsp::host::pointer_kind_of(p, dev) == lsp::host::kPtrDevice; }
+
+// Moves the grid origin of the phase records by dk frequencies: v += dk u
+// (mod 2^64), the same exact integer step the main kernel takes for its own
+// k, so the next frequency tile starts at bin k_b + dk with an exact phase.
+__global__ void __launch_bounds__(256) shift_origin_kernel(uint4* __restrict__ recA, int64_t n, uint32_t dk) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        uint4 a = recA[j];
+        const uint64_t u = ((uint64_t)a.y << 32) | a.x;
+        const uint64_t v = (((uint64_t)a.w << 32) | a.z) + (uint64_t)dk * u;
+        a.z = (uint32_t)v;
+        a.w = (uint32_t)(v >> 32);
+        recA[j] = a;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -69,12 +77,13 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     if (N_f < 0 || N_f >= (int64_t(1) << 31)) return LSP_ERR_INVALID_ARG;
     if (!std::isfinite(f_0) || !std::isfinite(df)) return LSP_ERR_NONFINITE;
     if (N_f == 0) return LSP_OK;
-    if (!t || !X || !P_out || !on_device(t) || !on_device(X) || !on_device(P_out)) return LSP_ERR_INVALID_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return LSP_ERR_CUDA;
     }
+    if (!t || !X || !P_out || !on_device(t, dev) || !on_device(X, dev) || !on_device(P_out, dev))
+        return LSP_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     int sms = 0;
     if (scratch_for(dev, &base, &sms) != cudaSuccess) {
@@ -92,24 +101,23 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     float* part = (float*)(base + kHeaderBytes + kRecordBytes);
 
     // Launch shape of the default (three-term recurrence) path: strips of 24
-    // frequencies; the N_t split fills the SMs and keeps chunks within
-    // kMaxChunk samples, but never needs more partial sums than fit.
-    lsp::MainShape s{};
-    s.mode = lsp::kModeRecur3;
-    s.F = 24;
-    const int64_t per_block = lsp::freqs_per_block(s.F);
-    s.nfb = (int)((N_f + per_block - 1) / per_block);
-    s.nf_pad = (int64_t)s.nfb * per_block;
-    const int64_t fit = (int64_t)(kPartialBytes / (size_t(4) * 4 * (size_t)s.nf_pad));
-    const int occ = lsp::main_occupancy(s.mode, s.F);
+    // frequencies, and an N_t split with chunks of at most kMaxChunk samples
+    // (the bound on the FP32 running sums that lsp_periodogram keeps), more
+    // where that fills the SMs.  The partial sums of `need` chunks fit the
+    // array for a limited number of frequencies, so the grid is evaluated in
+    // frequency tiles of at most that many bins, each a main launch and a
+    // finalize, with the records' phase origin moved exactly between tiles.
+    const int F = 24;
+    const int64_t per_block = lsp::freqs_per_block(F);
+    const int64_t need = (N_t + lsp::kMaxChunk - 1) / lsp::kMaxChunk;
+    const size_t row_bytes = size_t(4) * 4;  // four FP32 sums per (chunk, frequency)
+    int64_t tile = N_f;
+    if (need > 1) {
+        const int64_t blocks = (int64_t)(kPartialBytes / (row_bytes * (size_t)need * (size_t)per_block));
+        tile = std::min<int64_t>(N_f, blocks * per_block);
+    }
+    const int occ = lsp::main_occupancy(lsp::kModeRecur3, F);
     const int64_t slots = (int64_t)occ * (sms > 0 ? sms : 1);
-    int64_t split = (slots + s.nfb - 1) / s.nfb;
-    split = std::min<int64_t>(split, std::max<int64_t>(1, N_t / lsp::kMinChunk));
-    split = std::max<int64_t>(split, (N_t + lsp::kMaxChunk - 1) / lsp::kMaxChunk);
-    split = std::min<int64_t>(split, fit);
-    if (split < 2) split = 1;
-    s.chunk = (N_t + split - 1) / split;
-    s.split = (int)((N_t + s.chunk - 1) / s.chunk);
 
     // the shared array keeps the last call's contents: clear the status word
     // and the slice counter, which must start at zero
@@ -117,9 +125,31 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     if (e == cudaSuccess) e = lsp::launch_prep_stats(t, X, nullptr, N_t, 1, stats, status, sparts, counter, st);
     if (e == cudaSuccess)
         e = lsp::launch_prep_records(t, X, nullptr, N_t, 1, N_t, nullptr, nullptr, f_0, df, stats, recA, recB,
-                                     nullptr, nullptr, st);
-    if (e == cudaSuccess) e = lsp::launch_main(s, recA, recB, nullptr, N_t, N_f, f_0, df, part, P_out, st);
-    if (e == cudaSuccess && s.split > 1) e = lsp::launch_finalize(s, part, N_t, N_f, P_out, st);
+                                     nullptr, nullptr, st, nullptr, nullptr, status);
+    for (int64_t kb = 0; kb < N_f && e == cudaSuccess; kb += tile) {
+        const int64_t nf = std::min<int64_t>(tile, N_f - kb);
+        if (kb > 0) {
+            const int64_t g = std::min<int64_t>((N_t + 255) / 256, 4096);
+            shift_origin_kernel<<<(unsigned)g, 256, 0, st>>>(recA, N_t, (uint32_t)tile);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) break;
+        }
+        lsp::MainShape s{};
+        s.mode = lsp::kModeRecur3;
+        s.F = F;
+        s.nfb = (int)((nf + per_block - 1) / per_block);
+        s.nf_pad = (int64_t)s.nfb * per_block;
+        const int64_t fit = (int64_t)(kPartialBytes / (row_bytes * (size_t)s.nf_pad));
+        int64_t split = (slots + s.nfb - 1) / s.nfb;
+        split = std::min<int64_t>(split, std::max<int64_t>(1, N_t / lsp::kMinChunk));
+        split = std::min<int64_t>(split, fit);
+        split = std::max<int64_t>(split, need);  // need <= fit by the choice of the tile
+        if (split < 2) split = 1;
+        s.chunk = (N_t + split - 1) / split;
+        s.split = (int)((N_t + s.chunk - 1) / s.chunk);
+        e = lsp::launch_main(s, recA, recB, nullptr, N_t, nf, f_0, df, part, P_out + kb, st);
+        if (e == cudaSuccess && s.split > 1) e = lsp::launch_finalize(s, part, N_t, nf, P_out + kb, st);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return LSP_ERR_CUDA;

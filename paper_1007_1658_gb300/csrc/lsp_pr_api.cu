@@ -36,7 +36,13 @@ lsp_status lsp_press_rybicki(lsp_ctx* ctx, const double* t, const double* X, int
     DeviceGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
 
-    const bool t_dev = is_device_ptr(t), x_dev = is_device_ptr(X), p_dev = is_device_ptr(P_out);
+    bool t_dev = false, x_dev = false, p_dev = false;
+    {
+        lsp_status ws;
+        if ((ws = where(ctx, t, &t_dev)) != LSP_OK || (ws = where(ctx, X, &x_dev)) != LSP_OK ||
+            (ws = where(ctx, P_out, &p_dev)) != LSP_OK)
+            return ws;
+    }
     lsp_status rs;
     if ((rs = ensure(ctx, ctx->stats, sizeof(CurveStats))) != LSP_OK) return rs;
     const int slices = lsp::prep_stats_slices(1, N_t);

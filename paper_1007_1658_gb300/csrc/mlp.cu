@@ -186,9 +186,11 @@ __global__ void mean_kernel(int n, const float* __restrict__ v, float* __restric
     if (threadIdx.x == 0) *out = sh[0] / (float)n;
 }
 
-// Adam with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+// Adam with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t, and
+// decoupled weight decay wd (Loshchilov & Hutter 2019; wd = 0: plain Adam).
 __global__ void adam_kernel(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float b1, float b2, float c1, float c2, float eps) {
+                            float* __restrict__ v, float lr, float b1, float b2, float c1, float c2, float eps,
+                            float wd) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -196,7 +198,8 @@ __global__ void adam_kernel(int64_t n, float* __restrict__ p, const float* __res
     const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pi = p[i];
+    p[i] = pi - lr * (mi / c1) / (sqrtf(vi / c2) + eps) - (wd != 0.f ? lr * wd * pi : 0.f);
 }
 
 // Column mean and population standard deviation of n x 32 features (FP64 sums).
@@ -361,8 +364,8 @@ cudaError_t mlp_forward_backward(int H, int Bn, bool fp32, const float* params, 
 }
 
 cudaError_t mlp_adam(int64_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float c1,
-                     float c2, float eps, cudaStream_t st) {
-    adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, c1, c2, eps);
+                     float c2, float eps, float wd, cudaStream_t st) {
+    adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, p, g, m, v, lr, b1, b2, c1, c2, eps, wd);
     return cudaGetLastError();
 }
 

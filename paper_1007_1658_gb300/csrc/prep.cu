@@ -228,7 +228,8 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
                     const double* __restrict__ f0a, const double* __restrict__ dfa,
                     double f0s, double dfs, const CurveStats* __restrict__ stats,
                     uint4* __restrict__ recA, float4* __restrict__ recB, float2* __restrict__ recN,
-                    float* __restrict__ xout, const double* __restrict__ dy, float* __restrict__ qout) {
+                    float* __restrict__ xout, const double* __restrict__ dy, float* __restrict__ qout,
+                    int* __restrict__ status) {
     const int c = blockIdx.y;
     const int64_t b = off ? off[c] : 0;
     const int64_t e = off ? off[c + 1] : n0;
@@ -255,6 +256,11 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
             xh = (float)((X[j] - st.mean) * st.inv_sd) * q;
         } else {
             xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
+        }
+        // frac_turns64's range: beyond 2^52 turns the phase is not exact
+        if (!(fabs(tt * df) < 0x1p52) || !(fabs(tt * f0) < 0x1p52)) {
+            xh = __int_as_float(0x7fc00000);
+            if (status) atomicOr(status, kStatusPhaseRange);
         }
         recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
         recB[j] = make_float4(xh, cs, sn, __uint_as_float(du));
@@ -285,13 +291,13 @@ cudaError_t launch_prep_records(const double* t, const double* X, const int64_t*
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
                                 uint4* recA, float4* recB, float2* recN, float* xout, cudaStream_t st,
-                                const double* dy, float* qout) {
+                                const double* dy, float* qout, int* status) {
     int64_t bx = (max_n + 255) / 256;
     if (bx > 4096) bx = 4096;
     if (bx < 1) bx = 1;
     dim3 grid((unsigned)bx, (unsigned)n_curves);
     prep_records_kernel<<<grid, 256, 0, st>>>(t, X, off, n0, f0, df, f0_single, df_single, stats,
-                                              recA, recB, recN, xout, dy, qout);
+                                              recA, recB, recN, xout, dy, qout, status);
     return cudaGetLastError();
 }
 

@@ -116,6 +116,11 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_noise"):
         lib.lsp_noise.argtypes = [p, u64, i32, i32, i64, p]
         lib.lsp_noise.restype = ctypes.c_int
+    if hasattr(lib, "lsp_test_pointer_kind"):
+        lib.lsp_test_pointer_kind.argtypes = [i32, i32, i32]
+        lib.lsp_test_pointer_kind.restype = i32
+        lib.lsp_test_fail_allocation.argtypes = [p, i32]
+        lib.lsp_test_fail_allocation.restype = ctypes.c_int
 
 
 def options(**kw) -> lsp_options:
@@ -357,6 +362,10 @@ class Context:
     def fap_load(self, path):
         self._check(self._lib.lsp_fap_load(self.h, str(path).encode()))
 
+    def test_fail_allocation(self, n):
+        """lsp_test_fail_allocation: the n-th workspace allocation from now fails (0 cancels)."""
+        self._check(self._lib.lsp_test_fail_allocation(self.h, int(n)))
+
     def sync(self, timeout_s: float = -1.0):
         self._check(self._lib.lsp_sync(self.h, float(timeout_s)))
 
@@ -402,6 +411,11 @@ def periodogram_noalloc(t, X, f0, df, nf, out, stream=None):
     if st != OK:
         raise LspError(st, "lsp_periodogram_noalloc")
     return out
+
+
+def pointer_kind(memory_type, pointer_device, device):
+    """lsp_test_pointer_kind: 0 host (staged), 1 used in place, 2 another GPU (refused)."""
+    return int(load().lsp_test_pointer_kind(int(memory_type), int(pointer_device), int(device)))
 
 
 def grid(t_min, t_max, n, f_over, f_high):

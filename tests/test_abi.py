@@ -63,3 +63,18 @@ def test_default_options_and_bad_create(lib):
     h = ctypes.c_void_p()
     assert lib.lsp_create(ctypes.byref(h), 0, None, None) == lsp.ERR_INVALID_ARG
     assert not h.value
+
+
+def test_pointer_kind_decision(lib):
+    # cudaMemoryType: 0 unregistered host, 1 host (pinned/registered), 2 device, 3 managed
+    from paper_1007_1658_gb300 import lsp
+    HOST, IN_PLACE, OTHER_GPU = 0, 1, 2
+    for dev in (0, 1, 5):
+        assert lsp.pointer_kind(0, -2, dev) == HOST
+        assert lsp.pointer_kind(1, dev, dev) == HOST
+        assert lsp.pointer_kind(1, dev + 1, dev) == HOST  # pinned memory is reachable from every GPU
+        assert lsp.pointer_kind(2, dev, dev) == IN_PLACE
+        assert lsp.pointer_kind(3, dev, dev) == IN_PLACE
+        assert lsp.pointer_kind(3, dev + 1, dev) == IN_PLACE  # managed memory migrates on demand
+        for other in (dev + 1, dev + 2, 7 if dev != 7 else 6):
+            assert lsp.pointer_kind(2, other, dev) == OTHER_GPU
