@@ -281,22 +281,106 @@ def run_gpu(args, rank, world, dist):
                     "note": "prep + main (+ finalize), device pointers, median of 20"},
         "clocks": clk.summary(),
     }
-    if args.probe:
-        line["pipe_rates"] = pipe_rates(ctx, sms, peaks["sm_max_mhz"])
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(c, args.cpu_bins).items() if k != "seconds"}
-    if args.batch:
-        line["batched_mc"] = run_batch_bench(ctx, torch, dev, stream, args)
-        line["batched_mc"]["multi_rhs"] = run_mrhs_bench(torch, dev, stream)
-        if args.cpu_baseline and world == 1:
-            line["batched_mc"]["cpu_baseline"] = batch_cpu_sample()
+    # the legs below are ordered so that the last ones (the Monte-Carlo batch,
+    # the 65k-cadence precision comparison and the pipe rates) close the line
     if args.gls:
-        line["floating_mean"] = run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms)
+        line["floating_mean"] = _compact(run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms))
     if args.paper:
-        line["paper_shape"] = run_paper_shape(torch, dev, stream, args, peaks, sms)
+        line["paper_shape"] = _compact(run_paper_shape(torch, dev, stream, args, peaks, sms))
+    if args.batch:
+        line["multi_rhs"] = _compact(run_mrhs_bench(torch, dev, stream, args.mrhs_patterns, args.mrhs_real,
+                                                    tuple(int(g) for g in args.mrhs_groups.split(","))))
+    if args.probe:
+        line["pipe_rates"] = _compact(pipe_rates(ctx, sms, peaks["sm_max_mhz"]))
+    if args.cadence:
+        line["cadence_65k"] = _compact(run_cadence_bench(torch, dev, stream, args, peaks, peak_src, sms,
+                                                         args.cpu_baseline and world == 1))
+    if args.batch and args.mc:
+        mc = run_batch_bench(ctx, torch, dev, stream, args)
+        if args.cpu_baseline and world == 1:
+            cb = batch_cpu_sample()
+            # kept before the graph-vs-plain figures, which close the line
+            mc = dict([("cpu_baseline", {"curves_per_s": cb["value"], "terms_per_s": cb["terms_per_s"],
+                                         "cores": cb["cores"], "kind": cb["kind"], "sample": cb["sample"]})]
+                      + list(mc.items()))
+        line["batched_mc"] = _compact(mc)
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def _compact(v, digits=4):
+    """Floats rounded to `digits` significant digits (keeps the line short
+    enough that its last legs survive a log tail)."""
+    if isinstance(v, float):
+        return float("%.*g" % (digits, v)) if np.isfinite(v) else v
+    if isinstance(v, dict):
+        return {k: _compact(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_compact(x, digits) for x in v]
+    return v
+
+
+def run_cadence_bench(torch, dev, stream, args, peaks, peak_src, sms, with_oracle):
+    """Satellite-cadence precision stress (cadence_65k: 65,536 samples over
+    1300 d, 1e-3 sinusoids near 20 c/d, 318,500 frequencies, f t up to 3.2e4
+    turns): throughput of the default exact-phase kernel and of the paper's
+    single-precision phase (f*t - rintf(f*t), Sec. 4.3, hardware sin/cos), and
+    -- with the CPU baseline -- the error of each against the FP64 oracle on
+    sampled bins (256 random + 49 around each injected line), the oracle's
+    time on those bins being the CPU baseline of this workload."""
+    from paper_1007_1658_gb300 import lsp, synth
+    c = synth.cadence_65k()
+    terms = c.t.size * c.nf
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    t_d, X_d = d(c.t), d(c.X)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "cadence_65k: N_t = %d, N_f = %d (%.3g terms)" % (c.t.size, c.nf, terms)}
+    res = {}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, opts, per_clk, basis in (
+                ("fixed64", dict(), 128.0 / 6, "FMA pipe, 6 ops/term"),
+                ("naive_fp32", dict(phase_mode=lsp.PHASE_NAIVE_FP32), 16.0 / 2, "SFU, 2 ops/term")):
+            cctx = lsp.Context(dev.index or 0, stream=stream, timing=1, **opts)
+            P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
+            main = []
+
+            def fn():
+                cctx.periodogram(t_d, X_d, c.f0, c.df, c.nf, out=P_d)
+                main.append(cctx.last_timing()[1])
+            ms = _time_calls(torch, stream, fn, 2, max(3, args.steps // 2), flush)
+            cctx.sync(120.0)
+            main_ms = float(np.median(main[2:]))
+            peak = per_clk * sms * peaks["sm_max_mhz"] * 1e6
+            res[name] = P_d.cpu().numpy().astype(np.float64)
+            out[name] = {"ms": ms, "terms_per_s": terms / (ms * 1e-3), "main_ms": main_ms,
+                         "frac_of_roof": terms / (main_ms * 1e-3) / peak,
+                         "roof": "%s, %s sm_max_mhz" % (basis, peak_src)}
+            cctx.close()
+    out["clocks"] = clk.summary()
+    if with_oracle:
+        import oracle
+        rng = np.random.default_rng(99)
+        ks = set(rng.integers(0, c.nf, 256).tolist())
+        for f in c.signal_freqs:
+            k = int(round((f - c.f0) / c.df))
+            ks.update(range(max(0, k - 24), min(c.nf, k + 25)))
+        ks = np.array(sorted(ks), dtype=np.int64)
+        t0 = time.perf_counter()
+        ref = oracle.periodogram_at(c.t, c.X, c.f0 + ks * c.df)
+        sec = time.perf_counter() - t0
+        top = ks[np.argsort(-ref)[:10]]
+        rtop = np.sort(ref)[::-1][:10]
+        for name in ("fixed64", "naive_fp32"):
+            got = res[name][ks]
+            out[name]["max_abs_dP_over_maxP"] = float(np.max(np.abs(got - ref)) / ref.max())
+            out[name]["max_rel_err_top10"] = float(np.max(np.abs(res[name][top] - rtop) / rtop))
+        out["tolerance"] = 1e-4
+        out["cpu_baseline"] = {"terms_per_s": c.t.size * ks.size / sec, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": "%d sampled bins x all samples" % ks.size}
+    return out
 
 
 def pipe_rates(ctx, sms, sm_max_mhz):
@@ -305,9 +389,9 @@ def pipe_rates(ctx, sms, sm_max_mhz):
     they imply for each sin/cos mode at the SM count and maximum clock."""
     r = ctx.probe_pipes()
     g = sms * sm_max_mhz * 1e6 / 1e9
-    r["implied_roof_Gterms"] = {"MUFU (1 sin/cos pair per term)": r["sincos_per_clk_sm"] * g,
-                                "RECUR (8 FMA-pipe ops per term)": r["ffma_per_clk_sm"] / 8 * g,
-                                "RECUR3 (6 FMA-pipe ops per term)": r["ffma_per_clk_sm"] / 6 * g}
+    # roofs (Gterms/s) these rates imply: 1 sin/cos pair, 8 and 6 FMA-pipe ops per term
+    r["roof_Gterms"] = {"mufu": r["sincos_per_clk_sm"] * g, "recur": r["ffma_per_clk_sm"] / 8 * g,
+                        "recur3": r["ffma_per_clk_sm"] / 6 * g}
     return r
 
 
@@ -366,8 +450,7 @@ def run_paper_shape(torch, dev, stream, args, peaks, sms):
             P_d = torch.empty(c.nf, dtype=torch.float32, device=dev)
             fn = lambda: ctx.periodogram(t_d, X_d, c.f0, c.df, c.nf, out=P_d)
             ms = _time_calls(torch, stream, fn, 2, 3, flush)
-            row = {"N_t": int(c.t.size), "N_f": int(c.nf), "terms": c.terms, "gpu_ms": ms,
-                   "gpu_terms_per_s": c.terms / (ms * 1e-3)}
+            row = {"N_t": int(c.t.size), "gpu_ms": ms, "gpu_terms_per_s": c.terms / (ms * 1e-3)}
             if args.cpu_baseline and c.terms <= 2e8:
                 import oracle
                 t0 = time.perf_counter()
@@ -490,7 +573,7 @@ def batch_cpu_sample(n_sample=32, seed=1234):
             "kind": "oracle", "sample": "%d random curves of the 4096 (%.3g terms)" % (n_sample, terms)}
 
 
-def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64):
+def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64, groups=(1, 2, 4, 8)):
     """Many realizations per pattern (the surrogate's training shape: 256
     noise_batch patterns x 64 realizations, one lsp_batch call) for each
     multi-RHS group size; every result is bit-identical across group sizes."""
@@ -501,7 +584,7 @@ def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64):
     maxP = torch.empty(n_real * b.n, dtype=torch.float32, device=dev)
     arg = torch.empty(n_real * b.n, dtype=torch.int32, device=dev)
     out = []
-    for rhs in (1, 2, 4, 8):
+    for rhs in groups:
         mctx = lsp.Context(dev.index or 0, stream=stream, batch_rhs=rhs)
         with torch.cuda.stream(stream):
             mctx.batch(off, t, f0, df, nf, seed=1, n_real=n_real, maxP=maxP, argmax=arg)
@@ -582,11 +665,11 @@ def run_batch_bench(ctx, torch, dev, stream, args):
     bctx.close()
     pctx.close()
     return {"workload": "noise_batch: %d pure-noise curves, N_t log-U[200,20000], N_f = 2 N_t" % b.n,
-            "terms": b.terms, "graph_ms": batch_ms, "curves_per_s": b.n / (batch_ms * 1e-3),
-            "terms_per_s": b.terms / (batch_ms * 1e-3), "plain_ms": plain_ms,
-            "plain_curves_per_s": b.n / (plain_ms * 1e-3), "plain_terms_per_s": b.terms / (plain_ms * 1e-3),
-            "plain_launches": launches, "batch_launches": 1, "speedup_vs_plain": plain_ms / batch_ms,
-            "max_rel_diff_batch_vs_plain": agree, "clocks": clk.summary()}
+            "clocks": clk.summary(), "terms": b.terms, "plain_launches": launches, "batch_launches": 1,
+            "max_rel_diff_batch_vs_plain": agree, "plain_terms_per_s": b.terms / (plain_ms * 1e-3),
+            "terms_per_s": b.terms / (batch_ms * 1e-3), "plain_curves_per_s": b.n / (plain_ms * 1e-3),
+            "curves_per_s": b.n / (batch_ms * 1e-3), "plain_ms": plain_ms, "graph_ms": batch_ms,
+            "speedup_vs_plain": plain_ms / batch_ms}
 
 
 def main():
@@ -606,9 +689,16 @@ def main():
     ap.add_argument("--no-gls", dest="gls", action="store_false", help="skip the floating-mean periodogram leg")
     ap.add_argument("--no-paper", dest="paper", action="store_false", help="skip the paper-shape N_t sweep")
     ap.add_argument("--no-probe", dest="probe", action="store_false", help="skip the pipe-rate probe")
+    ap.add_argument("--no-cadence", dest="cadence", action="store_false",
+                    help="skip the 65k-cadence precision comparison (naive FP32 vs fixed-point phase)")
     ap.add_argument("--nf", type=int, default=0, help="override N_f (smaller profiling case)")
     ap.add_argument("--batch-curves", type=int, default=4096)
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--mrhs-patterns", type=int, default=256, help="multi-realization leg: sampling patterns")
+    ap.add_argument("--mrhs-real", type=int, default=64, help="multi-realization leg: realizations per pattern")
+    ap.add_argument("--mrhs-groups", default="1,2,4,8", help="multi-realization leg: group sizes to time")
+    ap.add_argument("--no-mc", dest="mc", action="store_false",
+                    help="skip the 4096-curve graph-vs-plain leg (keeps the multi-realization leg)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -48,6 +48,22 @@ class lsp_pipe_rates(ctypes.Structure):
                 ("ffma_per_clk_sm", ctypes.c_double), ("ffma2_lanes_per_clk_sm", ctypes.c_double)]
 
 
+class lsp_train_report(ctypes.Structure):
+    _fields_ = [("best_step", ctypes.c_int32), ("evaluations", ctypes.c_int32), ("val_loss_initial", ctypes.c_float),
+                ("val_loss_best", ctypes.c_float), ("train_loss_last", ctypes.c_float), ("gpu_ms", ctypes.c_float)]
+
+
+class lsp_train_opts(ctypes.Structure):
+    _fields_ = [("n_pat", ctypes.c_int32), ("n_rows", ctypes.c_int32), ("features", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("n_val_pat", ctypes.c_int32),
+                ("n_val_real", ctypes.c_int32), ("val_features", ctypes.c_void_p), ("val_counts", ctypes.c_void_p),
+                ("val_targets", ctypes.c_void_p), ("steps", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("warmup_steps", ctypes.c_int32), ("eval_every", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("weight_decay", ctypes.c_float), ("reserved0", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("val_history", ctypes.c_void_p), ("train_history", ctypes.c_void_p),
+                ("report", ctypes.POINTER(lsp_train_report))]
+
+
 def load():
     """Open liblsp.so (raises if it is missing: build it with __graft_entry__.build())."""
     global _lib
@@ -97,6 +113,8 @@ def _extra_prototypes(lib):
         lib.lsp_fap_features.argtypes = [p, i32, p, p, p, p, p, p]
         lib.lsp_fap_init.argtypes = [p, i32, u64, i32, p]
         lib.lsp_fap_train_step.argtypes = [p, i32, p, i32, p, p, p, ctypes.c_float, p]
+        lib.lsp_fap_train.argtypes = [p, ctypes.POINTER(lsp_train_opts)]
+        lib.lsp_fap_train.restype = ctypes.c_int
         lib.lsp_fap_gradients.argtypes = [p, i32, p, p, p, p, p]
         lib.lsp_fap_eval.argtypes = [p, i32, p, p, p]
         lib.lsp_fap_predict.argtypes = [p, i32, p, p, p, p, p, p]
@@ -316,6 +334,32 @@ class Context:
         self._check(self._lib.lsp_fap_train_step(self.h, int(rows.numel()), _ptr(rows), int(features.shape[0]),
                                                  _ptr(features), _ptr(counts), _ptr(targets), float(lr),
                                                  _ptr(loss_out)))
+
+    def fap_train(self, features, counts, targets, val_features, val_counts, val_targets, steps, batch=4096,
+                  lr=1e-3, lr_final=0.05, warmup_steps=0, weight_decay=0.0, eval_every=100, seed=0):
+        """lsp_fap_train: the whole training loop in the library.  features/counts
+        [n_pat][32]/[n_pat][2], targets [n_rows] (row r -> pattern r % n_pat),
+        val_targets [n_val_real][n_val_pat]; all device tensors.  Returns the
+        report as a dict with the validation and training-loss histories."""
+        n_val_real = int(val_targets.shape[0]) if val_targets.dim() == 2 else 1
+        passes = 2 + (int(steps) - 1) // int(eval_every) if eval_every > 0 else 2
+        vh = np.full(passes, np.nan, dtype=np.float32)
+        th = np.full(passes, np.nan, dtype=np.float32)
+        rep = lsp_train_report()
+        o = lsp_train_opts(n_pat=int(features.shape[0]), n_rows=int(targets.numel()), features=_ptr(features),
+                           counts=_ptr(counts), targets=_ptr(targets), n_val_pat=int(val_features.shape[0]),
+                           n_val_real=n_val_real, val_features=_ptr(val_features), val_counts=_ptr(val_counts),
+                           val_targets=_ptr(val_targets), steps=int(steps), batch=int(batch),
+                           warmup_steps=int(warmup_steps), eval_every=int(eval_every), lr=float(lr),
+                           lr_final=float(lr_final), weight_decay=float(weight_decay), reserved0=0, seed=int(seed),
+                           val_history=_ptr(vh), train_history=_ptr(th), report=ctypes.pointer(rep))
+        self._bind_stream()
+        self._check(self._lib.lsp_fap_train(self.h, ctypes.byref(o)))
+        e = rep.evaluations
+        d = {k: getattr(rep, k) for k, _ in lsp_train_report._fields_}
+        d["val_history"] = vh[:e].tolist()
+        d["train_history"] = th[:e].tolist()
+        return d
 
     def fap_gradients(self, features, counts, targets):
         B = int(features.shape[0])

@@ -1,9 +1,12 @@
 """Training and Monte-Carlo evaluation of the learned false-alarm surrogate.
 
 Orchestration only: the noise, the periodograms, their maxima, the pattern
-features and the network's forward, backward and Adam steps all run in
-liblsp.so's kernels (lsp_batch, lsp_fap_*); this module draws sampling
-patterns (synth.noise_batch), hands arrays to the C ABI and loops.
+features, the network and its whole training loop (minibatch draws, learning
+rate schedule, Adam, validation loss, choice of the kept weights) all run in
+liblsp.so (lsp_batch, lsp_fap_features, lsp_fap_train, lsp_fap_predict); this
+module draws sampling patterns (synth.noise_batch) and hands arrays to the C
+ABI.  The evaluation compares the library's quantiles with the empirical
+quantiles of brute-force Monte Carlo, the judge of the surrogate.
 
   python -m paper_1007_1658_gb300.surrogate [--quick] [--out model.lspfap] [--evaluate-only]
 
@@ -57,16 +60,13 @@ def mc_maxima(ctx: lsp.Context, pats: DevicePatterns, n_real: int, seed: int, ma
     return out
 
 
-def _pinball(q, y):
-    """Mean pinball loss of quantiles q [n, 9] against samples y [r, n] (host)."""
-    u = y[:, :, None] - q[None, :, :]
-    return float(np.mean(np.sum(np.maximum(LEVELS * u, (LEVELS - 1.0) * u), axis=2)))
-
-
-def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=2000, batch=4096, lr=1e-3, hidden=256,
-          seed=2024, n_val=2048, eval_every=100, verbose=True):
-    """Train the surrogate on n_patterns x n_real noise periodograms, keeping
-    the weights with the lowest pinball loss on n_val validation patterns."""
+def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=2000, batch=4096, lr=1e-3, lr_final=0.05,
+          warmup_steps=0, weight_decay=0.0, hidden=256, seed=2024, n_val=2048, val_real=8, eval_every=100,
+          verbose=True):
+    """Train the surrogate on n_patterns x n_real noise periodograms through
+    lsp_fap_train (the loop, the validation loss and the choice of the kept
+    weights all run in the library), validating on n_val patterns x val_real
+    realizations."""
     import torch
     dev = torch.device("cuda", ctx.device)
     t0 = time.perf_counter()
@@ -75,46 +75,32 @@ def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=2000, batch=4096, 
     pats = DevicePatterns(b, dev)
     vpats = DevicePatterns(vb, dev)
     t_gen = time.perf_counter() - t0
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     targets = mc_maxima(ctx, pats, n_real, seed=seed * 7919 + 1).reshape(-1).contiguous()
     ev[1].record()
-    vtargets = mc_maxima(ctx, vpats, 8, seed=seed * 7919 + 2).cpu().numpy().astype(np.float64)
+    vtargets = mc_maxima(ctx, vpats, val_real, seed=seed * 7919 + 2).contiguous()
     feats = ctx.fap_features(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
     vfeats = ctx.fap_features(vpats.t_off, vpats.t, vpats.f0, vpats.df, vpats.nf)
     ctx.fap_init(feats, hidden=hidden, seed=seed)
-    val = lambda: _pinball(ctx.fap_eval(vfeats, vpats.counts).cpu().numpy().astype(np.float64), vtargets)
-    best_loss, best_step, best_params = val(), 0, ctx.fap_get_params()
-    val_eq3 = best_loss
-    rng = np.random.default_rng(seed)
-    n_rows = n_real * n_patterns
-    losses = torch.zeros(steps, dtype=torch.float32, device=dev)
-    rows_d = torch.empty(batch, dtype=torch.int32, device=dev)
-    history = []
-    gpu_s_train = 0.0
-    for s in range(steps):
-        rows_d.copy_(torch.from_numpy(rng.integers(0, n_rows, batch, dtype=np.int32)))
-        # cosine decay to 5% of the initial rate
-        lr_s = lr * (0.05 + 0.95 * 0.5 * (1.0 + np.cos(np.pi * s / steps)))
-        ev[2].record()
-        ctx.fap_train_step(rows_d, feats, pats.counts, targets, lr_s, loss_out=losses[s:s + 1])
-        ev[3].record()
-        ev[3].synchronize()
-        gpu_s_train += ev[2].elapsed_time(ev[3]) / 1e3
-        if eval_every and (s % eval_every == eval_every - 1 or s == steps - 1):
-            v = val()
-            history.append((s + 1, round(v, 5)))
-            if v < best_loss:
-                best_loss, best_step, best_params = v, s + 1, ctx.fap_get_params()
-            if verbose:
-                print("step %5d  train %.4f  val %.4f  best %.4f@%d" % (s + 1, float(losses[s]), v, best_loss,
-                                                                      best_step), flush=True)
-    ctx.fap_set_params(best_params, hidden=hidden)
-    return {"patterns": n_patterns, "realizations": n_real, "periodograms": n_rows,
-            "terms": int(b.terms) * n_real, "steps": steps, "batch": batch, "lr": lr,
-            "gpu_s_data": ev[0].elapsed_time(ev[1]) / 1e3, "gpu_s_train": gpu_s_train,
-            "cpu_s_patterns": t_gen, "val_loss_eq3": val_eq3, "val_loss_best": best_loss, "best_step": best_step,
-            "val_history": history}
+    rep = ctx.fap_train(feats, pats.counts, targets, vfeats, vpats.counts, vtargets, steps=steps, batch=batch, lr=lr,
+                        lr_final=lr_final, warmup_steps=warmup_steps, weight_decay=weight_decay,
+                        eval_every=eval_every, seed=seed)
+    torch.cuda.synchronize(dev)
+    if verbose:
+        hist = zip(rep["val_history"], rep["train_history"])
+        for e, (v, tl) in enumerate(hist):
+            print("pass %3d  train %.4f  val %.4f" % (e, tl, v), flush=True)
+    steps_at = [0] + [min(steps, (e + 1) * eval_every) for e in range(rep["evaluations"] - 1)] if eval_every else [0, steps]
+    return {"patterns": n_patterns, "realizations": n_real, "periodograms": n_patterns * n_real,
+            "terms": int(b.terms) * n_real, "steps": steps, "batch": batch, "lr": lr, "lr_final": lr_final,
+            "warmup_steps": warmup_steps, "weight_decay": weight_decay, "val_patterns": n_val,
+            "val_realizations": val_real, "gpu_s_data": ev[0].elapsed_time(ev[1]) / 1e3,
+            "gpu_s_train": rep["gpu_ms"] / 1e3, "cpu_s_patterns": t_gen, "val_loss_eq3": rep["val_loss_initial"],
+            "val_loss_best": rep["val_loss_best"], "best_step": rep["best_step"],
+            "train_loss_last": rep["train_loss_last"],
+            "val_history": [(s_, round(v, 5)) for s_, v in zip(steps_at, rep["val_history"])],
+            "train_history": [(s_, round(v, 5)) for s_, v in zip(steps_at, rep["train_history"])]}
 
 
 def hidden_of(ctx: lsp.Context) -> int:
@@ -122,14 +108,6 @@ def hidden_of(ctx: lsp.Context) -> int:
     n = ctx.fap_get_params().size - 64
     # 32H + H + 2(H^2 + H) + 9H + 9 = 2H^2 + 44H + 9
     return int(round((-44 + np.sqrt(44 * 44 - 8 * (9 - n))) / 4))
-
-
-def eq3_quantiles(n_t, n_f):
-    """Eq. 3's quantiles of the largest of N_f independent noise peaks."""
-    n_t = np.asarray(n_t, np.float64)[:, None]
-    n_f = np.asarray(n_f, np.float64)[:, None]
-    a = -np.expm1(np.log(LEVELS[None, :]) / n_f)
-    return 0.5 * n_t * (-np.expm1(2.0 / (n_t - 3.0) * np.log(a)))
 
 
 def evaluate(ctx: lsp.Context, n_patterns=256, n_real=10000, seed=777001):
@@ -153,11 +131,15 @@ def evaluate(ctx: lsp.Context, n_patterns=256, n_real=10000, seed=777001):
     ctx32 = lsp.Context(ctx.device, mlp_fp32=1)
     ctx32.fap_set_params(ctx.fap_get_params(), hidden=hidden_of(ctx))
     q32 = ctx32.fap_predict(pats.t_off, pats.t, pats.f0, pats.df, pats.nf).cpu().numpy().astype(np.float64)
+    # Eq. 3's quantiles from the library's own head: a freshly initialized
+    # network has a zero output layer, and z = 0 is Eq. 3 exactly
+    feats = ctx32.fap_features(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
+    ctx32.fap_init(feats, hidden=4, seed=1)
+    q_eq3 = ctx32.fap_predict(pats.t_off, pats.t, pats.f0, pats.df, pats.nf).cpu().numpy().astype(np.float64)
     ctx32.close()
     m = np.sort(maxP.cpu().numpy().astype(np.float64), axis=0)
     idx = np.minimum(n_real - 1, np.ceil(LEVELS * n_real).astype(int) - 1)   # empirical quantiles
     q_mc = m[idx, :].T
-    q_eq3 = eq3_quantiles(np.diff(b.t_off), b.nf)
     rel_sur = np.abs(q_sur - q_mc) / q_mc
     rel_32 = np.abs(q32 - q_mc) / q_mc
     rel_eq3 = np.abs(q_eq3 - q_mc) / q_mc

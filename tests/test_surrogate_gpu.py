@@ -206,3 +206,70 @@ def test_quick_training_improves_on_eq3(lsp):
     tr = SU.train(ctx, n_patterns=2048, n_real=4, steps=150, batch=2048, n_val=256, eval_every=50, verbose=False)
     assert tr["val_loss_best"] < tr["val_loss_eq3"]
     ctx.close()
+
+
+def _train_set(ctx, n_pat, n_real, seed):
+    from paper_1007_1658_gb300 import surrogate as SU, synth
+    b = synth.noise_batch(n_curves=n_pat, seed=seed, nt_min=200, nt_max=4000, t_min=30.0, t_max=500.0)
+    pats = SU.DevicePatterns(b, torch.device("cuda", 0))
+    y = SU.mc_maxima(ctx, pats, n_real, seed=seed + 17).contiguous()
+    f = ctx.fap_features(pats.t_off, pats.t, pats.f0, pats.df, pats.nf)
+    return b, pats, f, y
+
+
+def test_lsp_fap_train_through_the_c_abi(lsp):
+    """The whole loop in the library (lsp_fap_train, called through ctypes):
+    its first validation loss is the pinball loss of Eq. 3's quantiles against
+    the validation maxima (recomputed here from the FP64 oracle's Eq. 3), the
+    kept weights end below it, the report agrees with the histories, and the
+    same seed gives the same weights."""
+    ctx = lsp.Context(0)
+    b, pats, feats, y = _train_set(ctx, 768, 4, 9100)
+    vb, vpats, vfeats, vy = _train_set(ctx, 96, 8, 9200)
+    params = []
+    reps = []
+    for _ in range(2):
+        ctx.fap_init(feats, hidden=64, seed=5)
+        rep = ctx.fap_train(feats, pats.counts, y.reshape(-1).contiguous(), vfeats, vpats.counts, vy, steps=240,
+                            batch=1024, lr=1e-3, warmup_steps=20, eval_every=40, seed=77)
+        params.append(ctx.fap_get_params())
+        reps.append(rep)
+    rep = reps[0]
+    assert np.array_equal(params[0], params[1]) and reps[0]["val_history"] == reps[1]["val_history"]
+    # pass before training: the untrained head is Eq. 3
+    n = np.diff(vb.t_off).astype(np.float64)
+    q = S.eq3_quantile(n[:, None], vb.nf.astype(np.float64)[:, None], np.array(S.LEVELS)[None, :])
+    yy = vy.cpu().numpy().astype(np.float64)  # [n_real][n_pat]
+    u = yy[:, :, None] - q[None, :, :]
+    lv = np.array(S.LEVELS)
+    ref = np.mean(np.sum(np.maximum(lv * u, (lv - 1.0) * u), axis=2))
+    assert abs(rep["val_loss_initial"] - ref) <= 1e-3 * ref, (rep["val_loss_initial"], ref)
+    assert rep["evaluations"] == 2 + (240 - 1) // 40 == len(rep["val_history"])
+    assert np.isnan(rep["train_history"][0]) and np.all(np.isfinite(rep["train_history"][1:]))
+    assert rep["val_loss_best"] == min(rep["val_history"])
+    assert rep["best_step"] in [0] + [min(240, 40 * (e + 1)) for e in range(rep["evaluations"] - 1)]
+    assert rep["val_loss_best"] < rep["val_loss_initial"]
+    # the context now holds the kept weights: evaluating them reproduces the best loss
+    qv = ctx.fap_eval(vfeats, vpats.counts).cpu().numpy().astype(np.float64)
+    u = yy[:, :, None] - qv[None, :, :]
+    got = np.mean(np.sum(np.maximum(lv * u, (lv - 1.0) * u), axis=2))
+    assert abs(got - rep["val_loss_best"]) <= 1e-4 * got
+    ctx.close()
+
+
+def test_lsp_fap_train_refuses_bad_schedules(lsp):
+    ctx = lsp.Context(0)
+    _, pats, feats, y = _train_set(ctx, 32, 2, 9300)
+    ctx.fap_init(feats, hidden=16, seed=1)
+    yy = y.reshape(-1).contiguous()
+    for kw in (dict(steps=0), dict(batch=0), dict(lr=0.0), dict(lr_final=1.5), dict(warmup_steps=50, steps=10),
+               dict(weight_decay=-1.0)):
+        args = dict(steps=10, batch=64, lr=1e-3)
+        args.update(kw)
+        with pytest.raises(lsp.LspError) as e:
+            ctx.fap_train(feats, pats.counts, yy, feats, pats.counts, y, **args)
+        assert e.value.status == lsp.ERR_INVALID_ARG
+    with pytest.raises(lsp.LspError) as e:  # host tables are refused
+        ctx.fap_train(feats.cpu(), pats.counts, yy, feats, pats.counts, y, steps=10, batch=64)
+    assert e.value.status == lsp.ERR_INVALID_ARG
+    ctx.close()
