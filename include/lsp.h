@@ -260,6 +260,40 @@ lsp_status lsp_grid(double t_min, double t_max, int64_t N_t, double F_over, doub
 lsp_status lsp_autotune(lsp_ctx *ctx, int64_t N_t, int64_t N_f, lsp_options *chosen);
 
 /*
+ * Autotuner of lsp_batch (the persistent Monte-Carlo launch of Sec. 6.2):
+ * times launch shapes on the caller's own batch description (curves, grids
+ * and n_real noise realizations, drawn from a fixed internal seed) and keeps
+ * the fastest whose per-periodogram maxima agree with the first shape's to
+ * 2e-5 (relative).  Shapes: for n_real = 1, the three-term recurrence with
+ * strips of F = 24 or 16 frequencies, tail strips of 8, 4 or none after a
+ * curve's last full block, and shared-memory tiles of 256, 128 or 512
+ * samples, and the angle-addition recurrence; for n_real > 1, realization
+ * groups R = 4 (F = 12 or 8, the three tiles), 2, 8 and 1.  The choice is
+ * remembered for this batch's size bucket (log2 of its terms per
+ * realization, log2 of its mean N_t, its realization count 1 / 2-3 / 4-7 / 8+):
+ * later lsp_batch calls in that bucket use it when the options leave the
+ * choice to the library (AUTO sin/cos, freqs_per_thread 0, batch_rhs 0).
+ * *chosen (may be NULL) receives the winner as options.  Arrays as lsp_batch
+ * (host or device).  Blocks; allocates temporary buffers.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+lsp_status lsp_autotune_batch(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, const double *t,
+                              const double *f_0, const double *df, const int64_t *N_f, int32_t n_real,
+                              lsp_options *chosen);
+
+/*
+ * The context's tuning table (lsp_autotune and lsp_autotune_batch entries)
+ * to and from a JSON file keyed by the GPU's name: {"lsp_tune": 1,
+ * "device": "<name>", "entries": [one object per line]}.  Loading merges the
+ * file's entries into the table (an entry replaces one of the same bucket)
+ * when the file was written on a GPU of the same name, and skips shapes this
+ * build does not have; *n_loaded (may be NULL) receives the count.
+ * Errors: INVALID_ARG (unreadable or not a tuning file).
+ */
+lsp_status lsp_tune_save(lsp_ctx *ctx, const char *path);
+lsp_status lsp_tune_load(lsp_ctx *ctx, const char *path, int32_t *n_loaded);
+
+/*
  * Pipe-rate probe: the per-SM, per-clock rates of the operations the
  * periodogram kernels are built from, measured on the context's GPU (Sec. 5.3
  * puts the GPU's lead down to its sin/cos throughput; these are the

@@ -37,6 +37,15 @@ int32_t lsp_test_pointer_kind(int32_t memory_type, int32_t pointer_device, int32
  */
 lsp_status lsp_test_fail_allocation(lsp_ctx *ctx, int32_t n);
 
+/*
+ * Launch shape of the context's last lsp_batch plan: shape[0..4] = kernel
+ * mode (1 hardware sin/cos, 2 angle-addition recurrence, 4 three-term
+ * recurrence, 5 its packed form), strip length F, realizations per pass R,
+ * tail-strip length (0: none) and samples per shared-memory tile.
+ * Errors: INVALID_ARG (null arguments, or no batch planned yet).
+ */
+lsp_status lsp_test_last_batch_shape(const lsp_ctx *ctx, int32_t shape[5]);
+
 #ifdef __cplusplus
 }
 #endif

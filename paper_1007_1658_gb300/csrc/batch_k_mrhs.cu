@@ -1,0 +1,27 @@
+// batch_k_mrhs.cu -- multi-realization batch kernels, three-term recurrence.
+#include "batch_kernels.cuh"
+
+namespace lsp {
+
+BatchFn mrhs_fn_recur3(int F, int R, int tile) {
+    using namespace dev;
+    if (tile == kTile) {
+        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur3, kTile>;
+        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, kTile>;
+        if (F == 8 && R == 2) return ls_mrhs_kernel<8, 2, kRecur3, kTile>;
+        if (F == 16 && R == 2) return ls_mrhs_kernel<16, 2, kRecur3, kTile>;
+        if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, kRecur3, kTile>;
+        return nullptr;
+    }
+    if (tile == 128) {
+        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, 128>;
+        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur3, 128>;
+    }
+    if (tile == 512) {
+        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, 512>;
+        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur3, 512>;
+    }
+    return nullptr;
+}
+
+}  // namespace lsp

@@ -1,0 +1,216 @@
+// batch_kernels.cuh -- the persistent kernels of lsp_batch as templates.
+//
+// Sec. 6.2 of the paper points at Monte-Carlo simulation of periodogram
+// statistics (e.g. the number of independent frequencies behind Eq. 3) as a
+// natural use of a GPU: many noise periodograms of the same sampling
+// pattern.  Here a batch of curves with uneven N_t and N_f (CSR layout), each
+// with one or many noise realizations, is evaluated by one persistent kernel:
+// CTAs take work items -- (realization, curve, block of kMainThreads*F
+// frequencies) -- from an atomic ticket in the order the host sorted them
+// (longest curve first, so the tail of the run is made of the shortest items),
+// run the same tile loop as the single-curve kernel over all samples of the
+// curve, finish Eq. 5-6 in registers, write P if asked, and fold the block's
+// largest P into the curve's maximum with one 64-bit atomicMax on
+// (bits of P) << 32 | ~k, which keeps the lowest k on ties.  Nothing ever
+// waits on another CTA: a CTA with no ticket left simply exits.
+// The templates are instantiated in several translation units (by sin/cos
+// mode and shape), each exporting a lookup from the runtime shape to its
+// kernels, so that the library compiles in parallel.
+#pragma once
+
+#include "ls_device.cuh"
+
+namespace lsp {
+
+using BatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, int64_t, int,
+                         const uint4*, const float4*, const float*, float*, const int64_t*, int64_t,
+                         unsigned long long*);
+
+// Kernel of a single-realization shape (nullptr when it is not built):
+// defaults (tail strips of 8 for F > 8, tiles of kTile) for every mode and
+// strip length, and for the three-term recurrence at F = 16 and 24 with x in
+// the records also tail strips of 0, 4, 8 and tiles of 128, 256, 512.
+BatchFn batch_fn_mufu(int F, bool xrec);
+BatchFn batch_fn_recur(int F, bool xrec);
+BatchFn batch_fn_recur3(int F, bool xrec, int tailF, int tile);
+BatchFn batch_fn_recur3x2(int F, bool xrec);
+// Multi-realization shapes (F, R) in {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)},
+// tiles of kTile; the three-term recurrence at (12, 4) and (8, 4) also with
+// tiles of 128 and 512.
+BatchFn mrhs_fn_recur3(int F, int R, int tile);
+BatchFn mrhs_fn_other(int mode, int F, int R);
+
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// One work item with strips of FF frequencies starting at k0: the tile loop
+// over all samples of the curve, Eq. 5-6, P written if asked; returns this
+// thread's largest (P bits << 32 | ~k) key.
+template <int FF, int MODE, bool XREC, class SM>
+__device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, int64_t b, int64_t e, int64_t N_f,
+                                                        const uint4* __restrict__ recA,
+                                                        const float4* __restrict__ recB, const float* x,
+                                                        float* P) {
+    Strip<FF, MODE> st;
+    st.zero();
+    // a strip that lies wholly beyond the grid (the padding of the item's last
+    // block) only helps stage the tiles: its warp, when all of it is padding,
+    // leaves its issue slots to the other CTAs on the SM
+    const bool live = k0 < (uint32_t)N_f;
+    if constexpr (XREC) {
+        // the single-curve kernel's loop: x from the records
+        for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
+            if (!live) return;
+#pragma unroll 2
+            for (int j = 0; j < n; ++j) {
+                const float4 B = bb[j];
+                st.add(a[j], B, B.x, k0);
+            }
+        });
+    } else {
+        for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
+            if (!live) return;
+#pragma unroll 2
+            for (int j = 0; j < n; ++j) st.add(a[j], bb[j], xs[j], k0);
+        });
+    }
+    const float n = (float)(e - b);
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int i = 0; i < FF; ++i) {
+        const uint32_t k = k0 + i;
+        if (k < (uint32_t)N_f) {
+            float xc, xs, cc, cs;
+            st.get(i, xc, xs, cc, cs);
+            const float p = periodogram_value(xc, xs, cc, cs, n);
+            if (P) P[k] = p;
+            best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
+        }
+    }
+    return best;
+}
+
+// TAILF: strip length of the tail items (0: none).  The frequencies of a curve
+// left over after its full blocks of kMainThreads*F run in blocks of
+// kMainThreads*TAILF, so at most kMainThreads*TAILF - 1 slots per curve are
+// padding.  TILE: samples per shared-memory tile.
+template <int F, int MODE, bool XREC, int TAILF, int TILE>
+__global__ void __launch_bounds__(kMainThreads)
+ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
+                const int64_t* __restrict__ off, const int64_t* __restrict__ nf, int64_t total, int n_curves,
+                const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ xr,
+                float* __restrict__ P_out, const int64_t* __restrict__ P_off, int64_t P_total,
+                unsigned long long* __restrict__ maxkey) {
+    __shared__ __align__(16) TileSmem<!XREC, TILE> sm;
+    __shared__ int s_item;
+    __shared__ unsigned long long s_red[kMainThreads / 32];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const int64_t b = off[w.curve], e = off[w.curve + 1];
+        const int64_t N_f = nf[w.curve];
+        const float* x = xr + (size_t)w.real * (size_t)total;
+        float* P = P_out ? P_out + (size_t)w.real * (size_t)P_total + P_off[w.curve] : nullptr;
+        unsigned long long best = 0ull;
+        bool tail = false;
+        if constexpr (TAILF > 0 && F > TAILF) {
+            if (w.pad < 0) {
+                // tail item: sub-block (-1 - pad) of kMainThreads*TAILF after fblock full blocks
+                const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) +
+                                    (uint32_t)(-1 - w.pad) * (kMainThreads * TAILF) + (uint32_t)threadIdx.x * TAILF;
+                best = batch_item<TAILF, MODE, XREC>(sm, k0, b, e, N_f, recA, recB, x, P);
+                tail = true;
+            }
+        }
+        if (!tail) {
+            const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+            best = batch_item<F, MODE, XREC>(sm, k0, b, e, N_f, recA, recB, x, P);
+        }
+        for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_down_sync(0xffffffffu, best, o));
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = s_red[0];
+            for (int q = 1; q < kMainThreads / 32; ++q) m = umax64(m, s_red[q]);
+            if (m) atomicMax(&maxkey[(size_t)w.real * n_curves + w.curve], m);
+        }
+    }
+}
+
+// Multi-RHS variant for many realizations of the same patterns: an item is
+// (curve, frequency block, group of up to R realizations starting at
+// w.real; w.pad = group size), and the group shares the phase, the
+// recurrence and CC/CS (MStrip).  Per (frequency, realization) the result is
+// the single-realization kernel's, bit for bit.
+template <int F, int R, int MODE, int TILE>
+__global__ void __launch_bounds__(kMainThreads)
+ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
+               const int64_t* __restrict__ off, const int64_t* __restrict__ nf, int64_t total, int n_curves,
+               const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ xr,
+               float* __restrict__ P_out, const int64_t* __restrict__ P_off, int64_t P_total,
+               unsigned long long* __restrict__ maxkey) {
+    __shared__ __align__(16) TileSmemN<R, TILE> sm;
+    __shared__ int s_item;
+    __shared__ unsigned long long s_red[R][kMainThreads / 32];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const int64_t b = off[w.curve], e = off[w.curve + 1];
+        const int64_t N_f = nf[w.curve];
+        const int nr = w.pad;
+        const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+        MStrip<F, R, MODE> st;
+        st.zero();
+        const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
+        for_each_tile_n<R>(sm, recA, recB, xr + (size_t)w.real * (size_t)total, total, nr, b, e,
+                           [&](const uint4* a, const float4* bb, const float (*xs)[TILE], int n) {
+                               if (!live) return;
+                               for (int j = 0; j < n; ++j) {
+                                   float x[R];
+#pragma unroll
+                                   for (int r = 0; r < R; ++r) x[r] = xs[r][j];
+                                   st.add(a[j], bb[j], x, k0);
+                               }
+                           });
+        const float n = (float)(e - b);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            unsigned long long best = 0ull;
+            float* P = (P_out && r < nr) ? P_out + (size_t)(w.real + r) * (size_t)P_total + P_off[w.curve] : nullptr;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                const uint32_t k = k0 + i;
+                if (k < (uint32_t)N_f && r < nr) {
+                    const float p = periodogram_value(st.xc[i][r], st.xs[i][r], st.cc[i], st.cs[i], n);
+                    if (P) P[k] = p;
+                    best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_down_sync(0xffffffffu, best, o));
+            if ((threadIdx.x & 31) == 0) s_red[r][threadIdx.x >> 5] = best;
+        }
+        __syncthreads();
+        if (threadIdx.x < R && (int)threadIdx.x < nr) {
+            const int r = threadIdx.x;
+            unsigned long long m = s_red[r][0];
+            for (int q = 1; q < kMainThreads / 32; ++q) m = umax64(m, s_red[r][q]);
+            if (m) atomicMax(&maxkey[(size_t)(w.real + r) * n_curves + w.curve], m);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace lsp

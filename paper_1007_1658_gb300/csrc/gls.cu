@@ -186,8 +186,10 @@ gls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB,
     const int64_t j1 = min(N, j0 + chunk);
     GStrip<F, MODE> st;
     st.zero();
+    const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
     for_each_tile_n<1>(sm, recA, recB, q, 0, 1, j0, j1,
                        [&](const uint4* a, const float4* b, const float (*qs)[kTile], int n) {
+                           if (!live) return;
 #pragma unroll 2
                            for (int j = 0; j < n; ++j) {
                                const float4 B = b[j];
@@ -257,8 +259,10 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
         GStrip<F, MODE> st;
         st.zero();
+        const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
         for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e,
                            [&](const uint4* a, const float4* bb, const float (*qs)[kTile], int n) {
+                               if (!live) return;
 #pragma unroll 2
                                for (int j = 0; j < n; ++j) {
                                    const float4 B = bb[j];

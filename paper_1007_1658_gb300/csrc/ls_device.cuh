@@ -330,30 +330,31 @@ struct MStrip {
 };
 
 // Double-buffered cp.async pipeline over the samples [j0, j1) in tiles of
-// kTile: stages the two 16-byte phase records of every sample and, when
-// `xr` is given, the sample values from that array; calls
-// body(a, b, x_or_null, n) once per tile with the tile in shared memory.
-// Every thread of the CTA must call it (it synchronizes the CTA).
-// NX rows of x values may come along: row r of a tile is xr[r * xstride + j].
-template <int NX>
+// TILE samples (kTile unless a kernel is built for another tile length):
+// stages the two 16-byte phase records of every sample and, when `xr` is
+// given, the sample values from that array; calls body(a, b, x, n) once per
+// tile with the tile in shared memory.  Every thread of the CTA must call it
+// (it synchronizes the CTA).  NX rows of x values may come along: row r of a
+// tile is xr[r * xstride + j].
+template <int NX, int TILE = kTile>
 struct TileSmemN {
-    uint4 A[2][kTile];
-    float4 B[2][kTile];
-    float X[2][NX > 0 ? NX : 1][NX > 0 ? kTile : 1];
+    uint4 A[2][TILE];
+    float4 B[2][TILE];
+    float X[2][NX > 0 ? NX : 1][NX > 0 ? TILE : 1];
 };
 
-template <bool XARR>
-using TileSmem = TileSmemN<XARR ? 1 : 0>;
+template <bool XARR, int TILE = kTile>
+using TileSmem = TileSmemN<XARR ? 1 : 0, TILE>;
 
-template <int NX, class Body>
-__device__ __forceinline__ void for_each_tile_n(TileSmemN<NX>& sm, const uint4* __restrict__ recA,
+template <int NX, int TILE, class Body>
+__device__ __forceinline__ void for_each_tile_n(TileSmemN<NX, TILE>& sm, const uint4* __restrict__ recA,
                                                 const float4* __restrict__ recB, const float* __restrict__ xr,
                                                 int64_t xstride, int nx_valid, int64_t j0, int64_t j1,
                                                 Body&& body) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int ntiles = j1 > j0 ? (int)((j1 - j0 + kTile - 1) / kTile) : 0;
+    const int ntiles = j1 > j0 ? (int)((j1 - j0 + TILE - 1) / TILE) : 0;
     auto stage = [&](int buf, int64_t jt) {
-        const int n = (int)min((int64_t)kTile, j1 - jt);
+        const int n = (int)min((int64_t)TILE, j1 - jt);
         for (int q = tid; q < n; q += nt) {
             cp_async16(&sm.A[buf][q], recA + jt + q);
             cp_async16(&sm.B[buf][q], recB + jt + q);
@@ -369,25 +370,24 @@ __device__ __forceinline__ void for_each_tile_n(TileSmemN<NX>& sm, const uint4* 
     if (ntiles > 0) stage(0, j0);
     cp_async_commit();
     for (int it = 0; it < ntiles; ++it) {
-        const int64_t jt = j0 + (int64_t)it * kTile;
-        if (it + 1 < ntiles) stage((it + 1) & 1, jt + kTile);
+        const int64_t jt = j0 + (int64_t)it * TILE;
+        if (it + 1 < ntiles) stage((it + 1) & 1, jt + TILE);
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        const int n = (int)min((int64_t)kTile, j1 - jt);
+        const int n = (int)min((int64_t)TILE, j1 - jt);
         body(sm.A[it & 1], sm.B[it & 1], sm.X[it & 1], n);
         __syncthreads();
     }
 }
 
-template <bool XARR, class Body>
-__device__ __forceinline__ void for_each_tile(TileSmem<XARR>& sm, const uint4* __restrict__ recA,
+template <bool XARR, int TILE, class Body>
+__device__ __forceinline__ void for_each_tile(TileSmem<XARR, TILE>& sm, const uint4* __restrict__ recA,
                                               const float4* __restrict__ recB, const float* __restrict__ xr,
                                               int64_t j0, int64_t j1, Body&& body) {
-    for_each_tile_n<XARR ? 1 : 0>(sm, recA, recB, xr, 0, XARR ? 1 : 0, j0, j1,
-                                  [&](const uint4* a, const float4* b, const float (*x)[XARR ? kTile : 1], int n) {
-                                      body(a, b, XARR ? x[0] : nullptr, n);
-                                  });
+    for_each_tile_n<XARR ? 1 : 0, TILE>(sm, recA, recB, xr, 0, XARR ? 1 : 0, j0, j1,
+                                        [&](const uint4* a, const float4* b, const float (*x)[XARR ? TILE : 1],
+                                            int n) { body(a, b, XARR ? x[0] : nullptr, n); });
 }
 
 }  // namespace dev

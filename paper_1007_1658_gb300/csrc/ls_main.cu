@@ -75,8 +75,10 @@ ls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, 
     const int64_t j1 = min(N, j0 + chunk);
     Strip<F, MODE> st;
     st.zero();
+    const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
     for_each_tile<false>(sm, recA, recB, nullptr, j0, j1,
                          [&](const uint4* a, const float4* b, const float*, int n) {
+                             if (!live) return;
 #pragma unroll 2
                              for (int j = 0; j < n; ++j) {
                                  const float4 B = b[j];

@@ -339,6 +339,16 @@ int32_t lsp_test_pointer_kind(int32_t memory_type, int32_t pointer_device, int32
     return pointer_kind(memory_type, pointer_device, device);
 }
 
+lsp_status lsp_test_last_batch_shape(const lsp_ctx* ctx, int32_t shape[5]) {
+    if (!ctx || !shape || !ctx->plan.valid) return LSP_ERR_INVALID_ARG;
+    shape[0] = ctx->plan.mode;
+    shape[1] = ctx->plan.F;
+    shape[2] = ctx->plan.R;
+    shape[3] = ctx->plan.tailF;
+    shape[4] = ctx->plan.tile;
+    return LSP_OK;
+}
+
 lsp_status lsp_test_fail_allocation(lsp_ctx* ctx, int32_t n) {
     if (!ctx || n < 0) return LSP_ERR_INVALID_ARG;
     ctx->fail_alloc_in = n;

@@ -22,11 +22,10 @@ void lsp::host::drop_plan(lsp_ctx* ctx) {
     ctx->plan = BatchPlan();
 }
 
-extern "C" {
-
-lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
-                     uint64_t seed, int32_t n_real, const double* f_0, const double* df, const int64_t* N_f,
-                     float* P_out, const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t,
+                                const double* X, uint64_t seed, int32_t n_real, const double* f_0, const double* df,
+                                const int64_t* N_f, float* P_out, const int64_t* P_off, float* maxP_out,
+                                int32_t* argmax_out, const BatchShape* forced) {
     if (!ctx) return LSP_ERR_INVALID_ARG;
     ctx->err.clear();
     ctx->timing_valid = false;
@@ -80,8 +79,34 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
     // strip lengths measured best on GB300 for each group size (256 patterns x 64 realizations)
     int F = R == 1 ? F1 : (R == 8 ? 4 : (R == 4 ? 12 : 16));
     // multi-realization strips: a strip length asked for replaces the default when that shape exists
-    if (R > 1 && ctx->opt.freqs_per_thread && lsp::mrhs_occupancy(mode, ctx->opt.freqs_per_thread, R) > 0)
+    if (R > 1 && ctx->opt.freqs_per_thread && lsp::mrhs_occupancy(mode, ctx->opt.freqs_per_thread, R, lsp::kTile) > 0)
         F = ctx->opt.freqs_per_thread;
+    int tailF = lsp::batch_default_tail(F), tile = lsp::kTile;
+    // a shape from lsp_autotune_batch for batches like this one, when the
+    // options leave the choice to the library
+    int64_t nf_total = 0;
+    for (int c = 0; c < n_curves; ++c) nf_total += nf[c];
+    const BatchShape* shape = forced;
+    if (!shape && ctx->opt.sincos_mode == LSP_SINCOS_AUTO && ctx->opt.freqs_per_thread == 0 && ctx->opt.batch_rhs == 0)
+        if (const BatchTuneEntry* te = tuned_batch(ctx, batch_bucket(n_curves, off[n_curves], nf_total, n_real)))
+            shape = &te->shape;
+    if (shape) {
+        mode = shape->mode;
+        F = shape->F;
+        R = std::min<int>(shape->R, n_real);
+        if (R > 1 && R < shape->R) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
+        tailF = shape->tailF;
+        tile = shape->tile;
+        if (R != shape->R) {  // fewer realizations than the tuned group: the default shape of this group
+            F = R == 1 ? 24 : (R == 8 ? 4 : (R == 4 ? 12 : 16));
+            tailF = lsp::batch_default_tail(F);
+            tile = lsp::kTile;
+        }
+    }
+    const bool xrec = n_real == 1;  // x travels inside the sample records
+    if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0)
+        return fail(ctx, LSP_ERR_UNSUPPORTED, "batch shape (mode %d, F %d, R %d, tail %d, tile %d) is not built", mode,
+                    F, R, tailF, tile);
     const int64_t per_block = lsp::freqs_per_block(F);
 
     // ---- device views of the inputs (host arrays are copied in, outside the graph) ----
@@ -121,20 +146,21 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
                                            ctx->b_head.p, ctx->b_seed.p, ctx->b_maxkey.p, ctx->b_items.p};
     BatchPlan& pl = ctx->plan;
     const bool same = pl.valid && pl.n_curves == n_curves && pl.n_real == n_real && pl.mode == mode &&
-                      pl.F == F && pl.R == R && pl.noise == noise && pl.ptrs == ptrs && pl.t_off == off &&
+                      pl.F == F && pl.R == R && pl.tailF == tailF && pl.tile == tile && pl.noise == noise &&
+                      pl.ptrs == ptrs && pl.t_off == off &&
                       pl.nf == nf && pl.f0 == f0v && pl.df == dfv && pl.p_off == poff;
     if (!same) {
         NvtxRange r("lsp_batch.plan");
         drop_plan(ctx);
         // work list: curves longest first (each item costs ~N_t), then blocks, then realizations;
         // with single-realization strips longer than the tail strip, the frequencies after a
-        // curve's last full block go to tail items of kMainThreads * kBatchTailF frequencies
+        // curve's last full block go to tail items of kMainThreads * tailF frequencies
         std::vector<int> order(n_curves);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
-        const bool tails = R == 1 && F > lsp::kBatchTailF;
-        const int64_t tail_block = lsp::freqs_per_block(lsp::kBatchTailF);
+        const bool tails = R == 1 && tailF > 0 && F > tailF;
+        const int64_t tail_block = lsp::freqs_per_block(tails ? tailF : 1);
         std::vector<lsp::BatchItem> items;
         for (int c : order) {
             const int64_t nfb = tails ? nf[c] / per_block : (nf[c] + per_block - 1) / per_block;
@@ -159,8 +185,7 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         std::vector<const void*> ptrs2 = ptrs;
         ptrs2.back() = ctx->b_items.p;
         (void)old_items;
-        const bool xrec = n_real == 1;  // x travels inside the sample records
-        const int occ = R > 1 ? lsp::mrhs_occupancy(mode, F, R) : lsp::batch_occupancy(mode, F, xrec);
+        const int occ = R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile) : lsp::batch_occupancy(mode, F, xrec, tailF, tile);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
 
         // capture the batch as one graph, on a private stream (the caller's
@@ -187,12 +212,13 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
             e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
                                        (float*)ctx->b_xr.p, (float4*)ctx->b_recB.p, cst);
         if (e == cudaSuccess && !items.empty() && R > 1)
-            e = lsp::launch_mrhs(mode, F, R, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+            e = lsp::launch_mrhs(mode, F, R, tile, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
                                  (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves, (const uint4*)ctx->b_recA.p,
                                  (const float4*)ctx->b_recB.p, (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
                                  (unsigned long long*)ctx->b_maxkey.p, cst);
         else if (e == cudaSuccess && !items.empty())
-            e = lsp::launch_batch(mode, F, xrec, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+            e = lsp::launch_batch(mode, F, xrec, tailF, tile, grid, (const lsp::BatchItem*)ctx->b_items.p,
+                                  (int)items.size(),
                                   (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves,
                                   (const uint4*)ctx->b_recA.p, (const float4*)ctx->b_recB.p,
                                   (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
@@ -216,6 +242,8 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
         pl.mode = mode;
         pl.F = F;
         pl.R = R;
+        pl.tailF = tailF;
+        pl.tile = tile;
         pl.noise = noise;
         pl.t_off = off;
         pl.nf = nf;
@@ -263,6 +291,15 @@ lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const
     }
     if (host_out) return lsp_sync(ctx, -1.0);
     return LSP_OK;
+}
+
+extern "C" {
+
+lsp_status lsp_batch(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                     uint64_t seed, int32_t n_real, const double* f_0, const double* df, const int64_t* N_f,
+                     float* P_out, const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+    return batch_run(ctx, n_curves, t_off, t, X, seed, n_real, f_0, df, N_f, P_out, P_off, maxP_out, argmax_out,
+                     nullptr);
 }
 
 lsp_status lsp_noise(lsp_ctx* ctx, uint64_t seed, int32_t curve, int32_t real, int64_t N, float* out) {

@@ -27,7 +27,7 @@ struct DevBuf {
 struct BatchPlan {
     bool valid = false;
     std::vector<const void*> ptrs;          // every pointer argument of the call
-    int n_curves = 0, n_real = 0, mode = 0, F = 0, R = 1;
+    int n_curves = 0, n_real = 0, mode = 0, F = 0, R = 1, tailF = 0, tile = 0;
     bool noise = false;
     std::vector<int64_t> t_off, nf, p_off;
     std::vector<double> f0, df;
@@ -40,6 +40,28 @@ struct BatchPlan {
 struct TuneEntry {
     int nt_bucket, nf_bucket;
     int sincos, F, split;
+    float ms;
+};
+
+// Launch shape of lsp_batch: kernel mode (kMode*), strip length, realizations
+// per pass, tail-strip length (0: none) and samples per shared-memory tile.
+struct BatchShape {
+    int mode, F, R, tailF, tile;
+};
+
+// Size bucket of a batch: log2 of its terms per realization, log2 of its
+// mean samples per curve, and its realization count (1, 2-3, 4-7, 8+).
+struct BatchBucket {
+    int terms, mean_nt, real;
+    bool operator==(const BatchBucket& o) const {
+        return terms == o.terms && mean_nt == o.mean_nt && real == o.real;
+    }
+};
+
+// One lsp_autotune_batch choice.
+struct BatchTuneEntry {
+    BatchBucket bucket;
+    BatchShape shape;
     float ms;
 };
 
@@ -76,6 +98,7 @@ struct lsp_ctx {
     lsp::host::BatchPlan plan;
     lsp::host::FapState fap;
     std::vector<lsp::host::TuneEntry> tune;  // lsp_autotune results, used by AUTO
+    std::vector<lsp::host::BatchTuneEntry> tune_batch;  // lsp_autotune_batch results, used by AUTO
     int* status_d = nullptr;  // device status word (OR of kStatus* bits)
     int* status_h = nullptr;  // pinned mirror
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -271,6 +294,16 @@ const TuneEntry* tuned(const lsp_ctx* ctx, int64_t N, int64_t N_f);
 
 // Release the cached batch graph.
 void drop_plan(lsp_ctx* ctx);
+
+BatchBucket batch_bucket(int n_curves, int64_t total_samples, int64_t total_freqs, int n_real);
+// lsp_autotune_batch entry for this bucket, or null.
+const BatchTuneEntry* tuned_batch(const lsp_ctx* ctx, const BatchBucket& b);
+
+// lsp_batch with an optional forced launch shape (the autotuner's candidates).
+lsp_status batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                     uint64_t seed, int32_t n_real, const double* f_0, const double* df, const int64_t* N_f,
+                     float* P_out, const int64_t* P_off, float* maxP_out, int32_t* argmax_out,
+                     const BatchShape* forced);
 
 }  // namespace host
 }  // namespace lsp

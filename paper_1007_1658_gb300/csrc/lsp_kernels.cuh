@@ -147,31 +147,38 @@ struct BatchItem {
     int32_t real;    // realization (first of the group for multi-RHS items)
     int32_t fblock;
     int32_t pad;     // multi-RHS items: realizations in the group; single-realization
-                     // items with F > 8: a negative value marks a tail item, sub-block
-                     // -1 - pad of kMainThreads*8 frequencies after fblock full blocks
+                     // items: a negative value marks a tail item, sub-block -1 - pad of
+                     // kMainThreads*tailF frequencies after fblock full blocks
 };
 
-// Strip length of the single-realization batch kernel's tail items.
+// Default strip length of the single-realization batch kernel's tail items:
+// the frequencies after a curve's last full block of kMainThreads*F run in
+// blocks of kMainThreads*kBatchTailF.  batch_default_tail(F) is it for F > 8,
+// else 0 (no tail items).
 constexpr int kBatchTailF = 8;
+int batch_default_tail(int F);
 
-int batch_occupancy(int mode, int F, bool x_in_records);
+// tailF, tile: tail-strip length (0: none) and samples per shared-memory tile
+// of the kernel; batch_occupancy is 0 when that shape is not built (the
+// defaults, batch_default_tail(F) and kTile, are built for every mode and F).
+int batch_occupancy(int mode, int F, bool x_in_records, int tailF, int tile);
 
 // x_in_records: every item's x is the x field of recB (one realization);
 // otherwise realization r reads xr[r][*].
-cudaError_t launch_batch(int mode, int F, bool x_in_records, int grid, const BatchItem* items, int n_items,
-                         unsigned* head,
-                         const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,
-                         const float4* recB, const float* xr, float* P_out, const int64_t* P_off, int64_t P_total,
-                         unsigned long long* maxkey, cudaStream_t st);
+cudaError_t launch_batch(int mode, int F, bool x_in_records, int tailF, int tile, int grid, const BatchItem* items,
+                         int n_items, unsigned* head, const int64_t* off, const int64_t* nf, int64_t total,
+                         int n_curves, const uint4* recA, const float4* recB, const float* xr, float* P_out,
+                         const int64_t* P_off, int64_t P_total, unsigned long long* maxkey, cudaStream_t st);
 
 // Multi-RHS batch: items carry a group of up to R realizations (real = first,
 // pad = count) sharing phases, recurrence and CC/CS; shapes (F, R) in
-// {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)}.
-int mrhs_occupancy(int mode, int F, int R);
-cudaError_t launch_mrhs(int mode, int F, int R, int grid, const BatchItem* items, int n_items, unsigned* head,
-                        const int64_t* off, const int64_t* nf, int64_t total, int n_curves, const uint4* recA,
-                        const float4* recB, const float* xr, float* P_out, const int64_t* P_off, int64_t P_total,
-                        unsigned long long* maxkey, cudaStream_t st);
+// {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)} with tiles of kTile, and for the
+// three-term recurrence (12, 4) and (8, 4) also with tiles of 128 and 512.
+int mrhs_occupancy(int mode, int F, int R, int tile);
+cudaError_t launch_mrhs(int mode, int F, int R, int tile, int grid, const BatchItem* items, int n_items,
+                        unsigned* head, const int64_t* off, const int64_t* nf, int64_t total, int n_curves,
+                        const uint4* recA, const float4* recB, const float* xr, float* P_out, const int64_t* P_off,
+                        int64_t P_total, unsigned long long* maxkey, cudaStream_t st);
 
 cudaError_t launch_unpack_max(const unsigned long long* maxkey, int64_t n, float* maxP, int32_t* argmax,
                               cudaStream_t st);

@@ -128,6 +128,12 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_autotune"):
         lib.lsp_autotune.argtypes = [p, i64, i64, ctypes.POINTER(lsp_options)]
         lib.lsp_autotune.restype = ctypes.c_int
+        lib.lsp_autotune_batch.argtypes = [p, i32, p, p, p, p, p, i32, ctypes.POINTER(lsp_options)]
+        lib.lsp_autotune_batch.restype = ctypes.c_int
+        lib.lsp_tune_save.argtypes = [p, ctypes.c_char_p]
+        lib.lsp_tune_save.restype = ctypes.c_int
+        lib.lsp_tune_load.argtypes = [p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
+        lib.lsp_tune_load.restype = ctypes.c_int
     if hasattr(lib, "lsp_probe_pipes"):
         lib.lsp_probe_pipes.argtypes = [p, ctypes.POINTER(lsp_pipe_rates)]
         lib.lsp_probe_pipes.restype = ctypes.c_int
@@ -139,6 +145,8 @@ def _extra_prototypes(lib):
         lib.lsp_test_pointer_kind.restype = i32
         lib.lsp_test_fail_allocation.argtypes = [p, i32]
         lib.lsp_test_fail_allocation.restype = ctypes.c_int
+        lib.lsp_test_last_batch_shape.argtypes = [p, p]
+        lib.lsp_test_last_batch_shape.restype = ctypes.c_int
 
 
 def options(**kw) -> lsp_options:
@@ -306,6 +314,31 @@ class Context:
         self._bind_stream()
         self._check(self._lib.lsp_autotune(self.h, int(n_t), int(n_f), ctypes.byref(o)))
         return {"sincos_mode": o.sincos_mode, "freqs_per_thread": o.freqs_per_thread, "split": o.split}
+
+    def autotune_batch(self, t_off, t, f0, df, nf, n_real=1):
+        """lsp_autotune_batch on this batch description: the chosen options as a dict."""
+        o = lsp_options()
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        self._bind_stream()
+        self._check(self._lib.lsp_autotune_batch(self.h, n, _ptr(t_off), _ptr(t), _ptr(f0), _ptr(df), _ptr(nf),
+                                                 int(n_real), ctypes.byref(o)))
+        return {"sincos_mode": o.sincos_mode, "freqs_per_thread": o.freqs_per_thread, "batch_rhs": o.batch_rhs}
+
+    def tune_save(self, path):
+        """lsp_tune_save: the tuning table as JSON."""
+        self._check(self._lib.lsp_tune_save(self.h, str(path).encode()))
+
+    def tune_load(self, path):
+        """lsp_tune_load: merge a tuning file; returns the number of entries taken."""
+        n = ctypes.c_int32(0)
+        self._check(self._lib.lsp_tune_load(self.h, str(path).encode(), ctypes.byref(n)))
+        return int(n.value)
+
+    def test_last_batch_shape(self):
+        """lsp_test_last_batch_shape: (mode, F, R, tail F, tile) of the last batch plan."""
+        a = np.zeros(5, dtype=np.int32)
+        self._check(self._lib.lsp_test_last_batch_shape(self.h, _ptr(a)))
+        return tuple(int(x) for x in a)
 
     def probe_pipes(self):
         """lsp_probe_pipes: measured per-SM, per-clock pipe rates as a dict."""

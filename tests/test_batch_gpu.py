@@ -14,7 +14,7 @@ import pytest
 from scipy import stats
 
 import oracle
-from tests.parity import TOL_ABS
+from tests.parity import TOL_ABS, assert_parity, assert_parity_with_degenerate_band
 
 pytestmark = pytest.mark.gpu
 
@@ -134,12 +134,18 @@ def test_edge_curves(ctx, lsp):
     f0 = np.array([0.1, 0.1, 0.05])
     df = np.array([0.1, 0.1, 0.05])
     nf = np.array([5, 0, 9], np.int64)
-    maxP, arg = ctx.batch(off, t, f0, df, nf, X=X)
+    P_off = np.array([0, 5, 5, 14], np.int64)
+    P = np.full(14, -1.0, np.float32)
+    maxP, arg = ctx.batch(off, t, f0, df, nf, X=X, P_out=P, P_off=P_off,
+                          maxP=np.empty(3, np.float32), argmax=np.empty(3, np.int32))
     assert maxP[1] == 0.0 and arg[1] == -1
     for c in (0, 2):
         s = slice(off[c], off[c + 1])
+        fr = f0[c] + np.arange(nf[c]) * df[c]
         ref = oracle.periodogram(t[s], X[s], f0[c], df[c], nf[c])
-        assert abs(maxP[c] - ref.max()) <= 1e-3 * max(1.0, ref.max())
+        got = P[P_off[c]:P_off[c] + nf[c]].astype(np.float64)
+        assert_parity_with_degenerate_band(got, ref, t[s], X[s], fr, what="curve %d" % c)
+        assert maxP[c] == got.max() and got[arg[c]] == got.max()
     with pytest.raises(lsp.LspError) as e:
         ctx.batch(off, t, f0, df, nf, X=np.array([1.0, 1.0, 0.2, 0.9, -1.3, 1.0, 2.0, 0.5]))
         ctx.sync(10.0)
@@ -215,15 +221,26 @@ def test_full_noise_batch_sampled_curves(ctx):
     b = synth.noise_batch(n_curves=4096)
     seed = 1234
     ctx.set_options()
-    maxP, argmax = ctx.batch(_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf), seed=seed)
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    P = torch.empty(int(P_off[-1]), dtype=torch.float32, device="cuda")
+    maxP, argmax = ctx.batch(_dev(b.t_off), _dev(b.t), _dev(b.f0), _dev(b.df), _dev(b.nf), seed=seed,
+                             P_out=P, P_off=_dev(P_off), maxP=torch.empty(b.n, dtype=torch.float32, device="cuda"),
+                             argmax=torch.empty(b.n, dtype=torch.int32, device="cuda"))
     ctx.sync(300.0)
     maxP = maxP.cpu().numpy()
     argmax = argmax.cpu().numpy()
+    P = P.cpu().numpy()
     n_t = np.diff(b.t_off)
     order = np.argsort(n_t, kind="stable")
-    picks = np.concatenate([order[:4], order[2046:2050], order[-4:-2]])
+    # the shortest, the middle and the longest curves: a batch item sums a whole
+    # curve in FP32, so the longest carry the largest rounding error
+    picks = np.concatenate([order[:4], order[2046:2050], order[-4:]])
     for c in picks:
         t, X = _oracle_noise_curve(b, seed, int(c), 0)
         ref = oracle.periodogram(t, X, b.f0[c], b.df[c], b.nf[c])
+        got = P[P_off[c]:P_off[c + 1]].astype(np.float64)
+        assert_parity(got, ref, what="curve %d (N_t = %d)" % (c, n_t[c]))
+        assert maxP[c] == got.max() and got[argmax[c]] == got.max(), c
         assert abs(maxP[c] - ref.max()) <= TOL_ABS * ref.max(), c
         assert ref[argmax[c]] >= ref.max() * (1 - 2 * TOL_ABS), c

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from oracle import press_rybicki as pr
-from tests.parity import assert_parity
+from tests.parity import assert_parity, assert_parity_with_degenerate_band
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,10 @@ def test_ragged_sizes_and_offsets(ctx, n, nf, j0):
         ref = pr.periodogram(t, X, j0, nf, df, macc)
         got = _pr(ctx, t, X, j0 * df, df, nf, macc)
         if n <= 2:
-            assert np.all(np.abs(got - ref) <= 1e-3 * max(1.0, ref.max()))
+            # the same bound away from the degenerate-term band (here the band is
+            # wider: the extirpolated tau sums carry the approximation's error)
+            assert_parity_with_degenerate_band(got, ref, t, X, (j0 + np.arange(nf)) * df, rel=2.0 ** -10,
+                                               kept_tol=1e-3, what="n=%d nf=%d j0=%d macc=%d" % (n, nf, j0, macc))
         else:
             assert_parity(got, ref, what="n=%d nf=%d j0=%d macc=%d" % (n, nf, j0, macc))
 
