@@ -629,6 +629,20 @@ def run_batch_bench(ctx, torch, dev, stream, args):
         bctx.sync(300.0)
     torch.cuda.synchronize(dev)
     batch_ms = e0.elapsed_time(e1) / reps
+    # the same batch after lsp_autotune_batch (launch shape chosen by timing on this batch)
+    tctx = lsp.Context(dev.index or 0, stream=stream)
+    with torch.cuda.stream(stream):
+        tctx.autotune_batch(off, t, f0, df, nf, n_real=1)
+        tctx.batch(off, t, f0, df, nf, seed=seed, maxP=maxP, argmax=arg)
+        tctx.sync(300.0)
+        tuned_shape = tctx.test_last_batch_shape()
+        e0.record(stream)
+        for r in range(reps):
+            tctx.batch(off, t, f0, df, nf, seed=seed + r, maxP=maxP, argmax=arg)
+        e1.record(stream)
+        tctx.sync(300.0)
+    tuned_ms = e0.elapsed_time(e1) / reps
+    tctx.close()
     # plain form: the same noise (realization 0 of seed 1234), one call per curve
     X = torch.empty(b.t.size, dtype=torch.float64, device=dev)
     tmp = torch.empty(int(np.diff(b.t_off).max()), dtype=torch.float32, device=dev)
@@ -668,6 +682,7 @@ def run_batch_bench(ctx, torch, dev, stream, args):
             "clocks": clk.summary(), "terms": b.terms, "plain_launches": launches, "batch_launches": 1,
             "max_rel_diff_batch_vs_plain": agree, "plain_terms_per_s": b.terms / (plain_ms * 1e-3),
             "terms_per_s": b.terms / (batch_ms * 1e-3), "plain_curves_per_s": b.n / (plain_ms * 1e-3),
+            "tuned_shape": dict(zip(("mode", "F", "R", "tailF", "tile"), tuned_shape)), "graph_ms_tuned": tuned_ms,
             "curves_per_s": b.n / (batch_ms * 1e-3), "plain_ms": plain_ms, "graph_ms": batch_ms,
             "speedup_vs_plain": plain_ms / batch_ms}
 

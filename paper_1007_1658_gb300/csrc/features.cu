@@ -53,7 +53,11 @@ ls_window_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         float* out = W + W_off[w.curve];
 #pragma unroll
         for (int i = 0; i < F; ++i)
-            if (k0 + i < (uint32_t)M) out[k0 + i] = (st.xc[i] * st.xc[i] + st.xs[i] * st.xs[i]) * inv;
+            if (k0 + i < (uint32_t)M) {
+                float xc, xs, cc, cs;
+                st.get(i, xc, xs, cc, cs);
+                out[k0 + i] = (xc * xc + xs * xs) * inv;
+            }
     }
 }
 

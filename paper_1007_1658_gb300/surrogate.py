@@ -60,13 +60,16 @@ def mc_maxima(ctx: lsp.Context, pats: DevicePatterns, n_real: int, seed: int, ma
     return out
 
 
-def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=2000, batch=4096, lr=1e-3, lr_final=0.05,
-          warmup_steps=0, weight_decay=0.0, hidden=256, seed=2024, n_val=2048, val_real=8, eval_every=100,
+def train(ctx: lsp.Context, n_patterns=65535, n_real=4, steps=4000, batch=4096, lr=3e-4, lr_final=0.05,
+          warmup_steps=100, weight_decay=3.0, hidden=256, seed=2024, n_val=2048, val_real=8, eval_every=100,
           verbose=True):
     """Train the surrogate on n_patterns x n_real noise periodograms through
     lsp_fap_train (the loop, the validation loss and the choice of the kept
     weights all run in the library), validating on n_val patterns x val_real
-    realizations."""
+    realizations.  Each pattern has only n_real noisy targets, so without
+    weight decay the network starts to fit the patterns' own noise after about
+    one epoch; the default decoupled weight decay keeps the training and
+    validation losses together to the end of the run."""
     import torch
     dev = torch.device("cuda", ctx.device)
     t0 = time.perf_counter()
@@ -170,10 +173,11 @@ def main():
         print(json.dumps({"evaluation": evaluate(ctx), "model": os.path.basename(args.out)}), flush=True)
         return
     if args.quick:
-        tr = train(ctx, n_patterns=4096, n_real=4, steps=args.steps or 400, batch=2048, n_val=512, eval_every=100)
+        tr = train(ctx, n_patterns=4096, n_real=4, steps=args.steps or 400, batch=2048, lr=1e-3, n_val=512,
+                   eval_every=100)
         jd = evaluate(ctx, n_patterns=64, n_real=2000)
     else:
-        tr = train(ctx, steps=args.steps or 2000)
+        tr = train(ctx, steps=args.steps or 4000)
         jd = evaluate(ctx)
     ctx.fap_save(args.out)
     print(json.dumps({"train": tr, "evaluation": jd, "model": os.path.basename(args.out)}), flush=True)

@@ -203,7 +203,8 @@ def test_quick_training_improves_on_eq3(lsp):
     validation pinball loss below Eq. 3's (the untrained network's)."""
     from paper_1007_1658_gb300 import surrogate as SU
     ctx = lsp.Context(0)
-    tr = SU.train(ctx, n_patterns=2048, n_real=4, steps=150, batch=2048, n_val=256, eval_every=50, verbose=False)
+    tr = SU.train(ctx, n_patterns=2048, n_real=4, steps=150, batch=2048, lr=1e-3, warmup_steps=10, n_val=256,
+                  eval_every=50, verbose=False)
     assert tr["val_loss_best"] < tr["val_loss_eq3"]
     ctx.close()
 
