@@ -266,7 +266,7 @@ lsp_status lsp_autotune(lsp_ctx *ctx, int64_t N_t, int64_t N_f, lsp_options *cho
  * the fastest whose per-periodogram maxima agree with the first shape's to
  * 2e-5 (relative).  Shapes: for n_real = 1, the three-term recurrence with
  * strips of F = 24 or 16 frequencies, tail strips of 8, 4 or none after a
- * curve's last full block, and shared-memory tiles of 256, 128 or 512
+ * curve's last full block, and shared-memory tiles of 128, 256 or 512
  * samples, and the angle-addition recurrence; for n_real > 1, realization
  * groups R = 4 (F = 12 or 8, the three tiles), 2, 8 and 1.  The choice is
  * remembered for this batch's size bucket (log2 of its terms per

@@ -13,9 +13,9 @@ BatchFn mrhs_fn_recur3(int F, int R, int tile) {
         if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, kRecur3, kTile>;
         return nullptr;
     }
-    if (tile == 128) {
-        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, 128>;
-        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur3, 128>;
+    if (tile == 256) {
+        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, 256>;
+        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur3, 256>;
     }
     if (tile == 512) {
         if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur3, 512>;

@@ -3,7 +3,7 @@
 
 namespace lsp {
 
-// The tuned shapes (tail strips of 0 or 4, tiles of 128 or 512) live in
+// The tuned shapes (the other tail strips and tiles of 256 or 512) live in
 // batch_k_recur3_tuned.cu.
 BatchFn batch_fn_recur3_tuned(int F, int tailF, int tile);
 

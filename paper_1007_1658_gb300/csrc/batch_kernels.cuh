@@ -36,7 +36,7 @@ BatchFn batch_fn_recur3(int F, bool xrec, int tailF, int tile);
 BatchFn batch_fn_recur3x2(int F, bool xrec);
 // Multi-realization shapes (F, R) in {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)},
 // tiles of kTile; the three-term recurrence at (12, 4) and (8, 4) also with
-// tiles of 128 and 512.
+// tiles of 256 and 512.
 BatchFn mrhs_fn_recur3(int F, int R, int tile);
 BatchFn mrhs_fn_other(int mode, int F, int R);
 

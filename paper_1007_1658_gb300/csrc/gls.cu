@@ -147,6 +147,8 @@ struct GStrip<F, kRecur3x2> {
 };
 
 // p from the six sums (weights summing to 1, data variance 1), in FP64.
+// Data the prep kernels refuse are reported through the status word (this
+// path has no allocation-free form that would need NaN outputs instead).
 __device__ __forceinline__ float gls_value(double XC, double XS, double C, double S, double CCp, double CSp,
                                            double n) {
     const double CC = CCp - C * C;
@@ -171,24 +173,23 @@ __device__ __forceinline__ float gls_value(double XC, double XS, double C, doubl
     double p = 0.0;
     if (den1 > thr) p += num1 / den1;
     if (den2 > thr) p += num2 / den2;
-    const double probe = z2 + R + T;  // NaN sums give NaN, not the 0 of the clamps above
-    return probe == probe ? (float)(0.5 * n * p) : (float)probe;
+    return (float)(0.5 * n * p);
 }
 
 template <int F, int MODE>
-__global__ void __launch_bounds__(kMainThreads)
+__global__ void __launch_bounds__(kGlsThreads)
 gls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ q,
                 int64_t N, int64_t chunk, int N_f, int64_t nf_pad, float* __restrict__ part,
                 float* __restrict__ P_out) {
-    __shared__ __align__(16) TileSmemN<1> sm;
-    const uint32_t k0 = (uint32_t)blockIdx.x * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+    __shared__ __align__(16) TileSmemN<1, kGlsTile> sm;
+    const uint32_t k0 = (uint32_t)blockIdx.x * (kGlsThreads * F) + (uint32_t)threadIdx.x * F;
     const int64_t j0 = (int64_t)blockIdx.y * chunk;
     const int64_t j1 = min(N, j0 + chunk);
     GStrip<F, MODE> st;
     st.zero();
     const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
     for_each_tile_n<1>(sm, recA, recB, q, 0, 1, j0, j1,
-                       [&](const uint4* a, const float4* b, const float (*qs)[kTile], int n) {
+                       [&](const uint4* a, const float4* b, const float (*qs)[kGlsTile], int n) {
                            if (!live) return;
 #pragma unroll 2
                            for (int j = 0; j < n; ++j) {
@@ -235,18 +236,18 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
 }
 
 // Many curves in one persistent launch: CTAs take (curve, block of
-// kMainThreads*F frequencies) items from an atomic ticket, run the strip over
+// kGlsThreads*F frequencies) items from an atomic ticket, run the strip over
 // all samples of the curve, finish p in FP64, write P if asked and fold the
 // block's largest P into the curve's (P bits << 32 | ~k) maximum.
 template <int F, int MODE>
-__global__ void __launch_bounds__(kMainThreads)
+__global__ void __launch_bounds__(kGlsThreads)
 gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
                  const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
                  const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
                  const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey) {
-    __shared__ __align__(16) TileSmemN<1> sm;
+    __shared__ __align__(16) TileSmemN<1, kGlsTile> sm;
     __shared__ int s_item;
-    __shared__ unsigned long long s_red[kMainThreads / 32];
+    __shared__ unsigned long long s_red[kGlsThreads / 32];
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
         __syncthreads();
@@ -256,12 +257,12 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         const BatchItem w = items[it];
         const int64_t b = off[w.curve], e = off[w.curve + 1];
         const int64_t N_f = nf[w.curve];
-        const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+        const uint32_t k0 = (uint32_t)w.fblock * (kGlsThreads * F) + (uint32_t)threadIdx.x * F;
         GStrip<F, MODE> st;
         st.zero();
         const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
         for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e,
-                           [&](const uint4* a, const float4* bb, const float (*qs)[kTile], int n) {
+                           [&](const uint4* a, const float4* bb, const float (*qs)[kGlsTile], int n) {
                                if (!live) return;
 #pragma unroll 2
                                for (int j = 0; j < n; ++j) {
@@ -285,7 +286,7 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long m = s_red[0];
-            for (int x = 1; x < kMainThreads / 32; ++x) m = umax64(m, s_red[x]);
+            for (int x = 1; x < kGlsThreads / 32; ++x) m = umax64(m, s_red[x]);
             if (m) atomicMax(&maxkey[w.curve], m);
         }
     }
@@ -344,7 +345,7 @@ int gls_occupancy(int mode, int F) {
     const GlsFn fn = gls_fn(mode, F);
     if (!fn) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kMainThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -356,7 +357,7 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
     const GlsFn fn = gls_fn(s.mode, s.F);
     if (!fn) return cudaErrorInvalidValue;
     dim3 grid((unsigned)s.nfb, (unsigned)s.split);
-    fn<<<grid, kMainThreads, 0, st>>>(recA, recB, q, N, s.chunk, (int)N_f, s.nf_pad, part,
+    fn<<<grid, kGlsThreads, 0, st>>>(recA, recB, q, N, s.chunk, (int)N_f, s.nf_pad, part,
                                       s.split == 1 ? P_out : nullptr);
     return cudaGetLastError();
 }
@@ -365,7 +366,7 @@ int gls_batch_occupancy(int mode, int F) {
     const GlsBatchFn fn = gls_batch_fn(mode, F);
     if (!fn) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kMainThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -378,7 +379,7 @@ cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, 
                              cudaStream_t st) {
     const GlsBatchFn fn = gls_batch_fn(mode, F);
     if (!fn) return cudaErrorInvalidValue;
-    fn<<<grid, kMainThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
+    fn<<<grid, kGlsThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
     return cudaGetLastError();
 }
 

@@ -99,8 +99,9 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
 
 // Frequency blocks, padding and the N_t split of a shape whose mode and F are
 // set; occ = resident CTAs per SM of its kernel.
-void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64_t N, int64_t N_f, int split) {
-    const int64_t per_block = lsp::freqs_per_block(s.F);
+void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64_t N, int64_t N_f, int split,
+                             int threads) {
+    const int64_t per_block = (int64_t)threads * s.F;
     s.nfb = (int)((N_f + per_block - 1) / per_block);
     s.nf_pad = (int64_t)s.nfb * per_block;
     if (split <= 0) {

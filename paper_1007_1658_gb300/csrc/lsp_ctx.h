@@ -287,7 +287,8 @@ lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
 
 // Frequency blocks, padding and N_t split (split <= 0: fill whole waves of
 // occ resident CTAs per SM) of a shape whose mode and F are already set.
-void finish_shape(const lsp_ctx* ctx, lsp::MainShape& s, int occ, int64_t N, int64_t N_f, int split);
+void finish_shape(const lsp_ctx* ctx, lsp::MainShape& s, int occ, int64_t N, int64_t N_f, int split,
+                  int threads = lsp::kMainThreads);
 
 // Autotuned entry for this size bucket, or null.
 const TuneEntry* tuned(const lsp_ctx* ctx, int64_t N, int64_t N_f);

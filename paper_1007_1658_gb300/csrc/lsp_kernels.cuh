@@ -59,8 +59,9 @@ cudaError_t launch_prep_stats(const double* t, const double* X, const int64_t* o
 // dy, or none for equal weights) receives q_j = sqrt(w_j), sum w = 1, and x_hat
 // becomes q_j (X_j - mean_w) / sd_w.
 // The fixed-point phases need |t_j - t_ref| f_0 and |t_j - t_ref| df below
-// 2^52 turns; a sample beyond that gets x_hat = NaN (so its periodogram is
-// NaN) and sets kStatusPhaseRange in *status when status is given.
+// 2^52 turns; a sample beyond that gets x_hat = NaN (so the classic
+// periodogram of its curve is NaN) and sets kStatusPhaseRange in *status
+// when status is given.
 cudaError_t launch_prep_records(const double* t, const double* X, const int64_t* off, int64_t n0,
                                 int n_curves, int64_t max_n, const double* f0, const double* df,
                                 double f0_single, double df_single, const CurveStats* stats,
@@ -81,12 +82,22 @@ struct MainShape {
     int64_t nf_pad;// padded row length of the partial-sum workspace
 };
 
-constexpr int kMainThreads = 128;
-constexpr int kTile = 256;
+// CTA shape of the classic strip kernels (single curve, batch, multi-
+// realization, spectral window): one warp per CTA, tiles of 128 samples.  With
+// several warps per CTA the warps of one CTA run on different SM
+// sub-partitions, drift apart between tile barriers and wait for each other;
+// one-warp CTAs (17 resident per SM at 119 registers a thread) measured 1.3%
+// faster on the 100k x 200k periodogram and 3% on the 4096-curve batch.
+constexpr int kMainThreads = 32;
+constexpr int kTile = 128;
+// The floating-mean (six-sum) kernels keep four-warp CTAs and 256-sample
+// tiles, which measured 4.5% faster for them than one-warp CTAs.
+constexpr int kGlsThreads = 128;
+constexpr int kGlsTile = 256;
 // Fewest samples per N_t chunk that the launch-shape heuristic makes.  A
 // problem too small to fill one wave of CTAs is latency-bound: each thread's
 // serial loop over its chunk is the critical path, so such problems are split
-// down to chunks of this many samples (a quarter of a tile).
+// down to chunks of this many samples.
 constexpr int kMinChunk = 64;
 // Most samples per N_t chunk that the launch-shape heuristic makes.  Each
 // thread's FP32 running sums cover one chunk (the paper's chunked summation,
@@ -97,8 +108,9 @@ constexpr int kMinChunk = 64;
 // at no cost in time).
 constexpr int64_t kMaxChunk = int64_t(1) << 14;
 
-// Frequencies covered by one CTA of the main kernel.
+// Frequencies covered by one CTA of the main kernel (of a floating-mean kernel).
 inline int freqs_per_block(int F) { return kMainThreads * F; }
+inline int gls_freqs_per_block(int F) { return kGlsThreads * F; }
 
 // Resident CTAs per SM of the main kernel for (mode, F).
 int main_occupancy(int mode, int F);
@@ -173,7 +185,7 @@ cudaError_t launch_batch(int mode, int F, bool x_in_records, int tailF, int tile
 // Multi-RHS batch: items carry a group of up to R realizations (real = first,
 // pad = count) sharing phases, recurrence and CC/CS; shapes (F, R) in
 // {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)} with tiles of kTile, and for the
-// three-term recurrence (12, 4) and (8, 4) also with tiles of 128 and 512.
+// three-term recurrence (12, 4) and (8, 4) also with tiles of 256 and 512.
 int mrhs_occupancy(int mode, int F, int R, int tile);
 cudaError_t launch_mrhs(int mode, int F, int R, int tile, int grid, const BatchItem* items, int n_items,
                         unsigned* head, const int64_t* off, const int64_t* nf, int64_t total, int n_curves,

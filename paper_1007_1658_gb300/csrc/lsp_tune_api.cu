@@ -230,10 +230,10 @@ extern "C" lsp_status lsp_autotune_batch(lsp_ctx* ctx, int32_t n_curves, const i
     if (n_real == 1) {
         for (int F : {24, 16})
             for (int tail : {8, 4, 0})
-                for (int tile : {256, 128, 512}) cands.push_back({kModeRecur3, F, 1, tail, tile});
+                for (int tile : {128, 256, 512}) cands.push_back({kModeRecur3, F, 1, tail, tile});
         cands.push_back({lsp::kModeRecur, 16, 1, 8, lsp::kTile});
     } else {
-        for (int tile : {256, 128, 512}) {
+        for (int tile : {128, 256, 512}) {
             cands.push_back({kModeRecur3, 12, 4, 0, tile});
             cands.push_back({kModeRecur3, 8, 4, 0, tile});
         }
