@@ -86,7 +86,7 @@ struct MainShape {
 // realization, spectral window): one warp per CTA, tiles of 128 samples.  With
 // several warps per CTA the warps of one CTA run on different SM
 // sub-partitions, drift apart between tile barriers and wait for each other;
-// one-warp CTAs (17 resident per SM at 119 registers a thread) measured 1.3%
+// one-warp CTAs (16 resident per SM at 121 registers a thread) measured 1.3%
 // faster on the 100k x 200k periodogram and 3% on the 4096-curve batch.
 constexpr int kMainThreads = 32;
 constexpr int kTile = 128;
