@@ -64,13 +64,9 @@ __device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, in
     const bool live = k0 < (uint32_t)N_f;
     if constexpr (XREC) {
         // the single-curve kernel's loop: x from the records
+        constexpr int T = sizeof(sm.A[0]) / sizeof(uint4);  // the tile length of this kernel
         for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
-            if (!live) return;
-#pragma unroll 2
-            for (int j = 0; j < n; ++j) {
-                const float4 B = bb[j];
-                st.add(a[j], B, B.x, k0);
-            }
+            if (live) strip_tile<T>(st, a, bb, n, k0);
         });
     } else {
         for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
@@ -151,6 +147,55 @@ ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __re
 // w.real; w.pad = group size), and the group shares the phase, the
 // recurrence and CC/CS (MStrip).  Per (frequency, realization) the result is
 // the single-realization kernel's, bit for bit.
+// Tile of the multi-realization kernel: the records as in TileSmemN, and the
+// x values of a sample's R realizations side by side (X[buf][j][0..R-1]), so
+// that R = 4 realizations come in one 128-bit load.  Measured with one-warp
+// CTAs: 156.1 -> 148.2 ms for 256 patterns x 64 realizations at R = 4 (with
+// four-warp CTAs the same layout had measured slower).
+template <int R, int TILE>
+struct TileSmemX {
+    uint4 A[2][TILE];
+    float4 B[2][TILE];
+    float X[2][TILE][R];
+};
+
+// The double-buffered cp.async pipeline of for_each_tile_n for TileSmemX:
+// realization r of sample j comes from xr[r * xstride + j]; realizations
+// r >= nx_valid (the last group's missing ones) read as 0.
+template <int R, int TILE, class Body>
+__device__ __forceinline__ void for_each_tile_x(TileSmemX<R, TILE>& sm, const uint4* __restrict__ recA,
+                                                const float4* __restrict__ recB, const float* __restrict__ xr,
+                                                int64_t xstride, int nx_valid, int64_t j0, int64_t j1, Body&& body) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntiles = j1 > j0 ? (int)((j1 - j0 + TILE - 1) / TILE) : 0;
+    auto stage = [&](int buf, int64_t jt) {
+        const int n = (int)min((int64_t)TILE, j1 - jt);
+        for (int q = tid; q < n; q += nt) {
+            cp_async16(&sm.A[buf][q], recA + jt + q);
+            cp_async16(&sm.B[buf][q], recB + jt + q);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r < nx_valid)
+                    cp_async4(&sm.X[buf][q][r], xr + (size_t)r * (size_t)xstride + jt + q);
+                else
+                    sm.X[buf][q][r] = 0.f;
+            }
+        }
+    };
+    if (ntiles > 0) stage(0, j0);
+    cp_async_commit();
+    for (int it = 0; it < ntiles; ++it) {
+        const int64_t jt = j0 + (int64_t)it * TILE;
+        if (it + 1 < ntiles) stage((it + 1) & 1, jt + TILE);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int n = (int)min((int64_t)TILE, j1 - jt);
+        body(sm.A[it & 1], sm.B[it & 1], sm.X[it & 1], n);
+        __syncthreads();
+    }
+}
+
 template <int F, int R, int MODE, int TILE>
 __global__ void __launch_bounds__(kMainThreads)
 ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
@@ -158,7 +203,7 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
                const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ xr,
                float* __restrict__ P_out, const int64_t* __restrict__ P_off, int64_t P_total,
                unsigned long long* __restrict__ maxkey) {
-    __shared__ __align__(16) TileSmemN<R, TILE> sm;
+    __shared__ __align__(16) TileSmemX<R, TILE> sm;
     __shared__ int s_item;
     __shared__ unsigned long long s_red[R][kMainThreads / 32];
     for (;;) {
@@ -175,16 +220,24 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
         MStrip<F, R, MODE> st;
         st.zero();
         const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
-        for_each_tile_n<R>(sm, recA, recB, xr + (size_t)w.real * (size_t)total, total, nr, b, e,
-                           [&](const uint4* a, const float4* bb, const float (*xs)[TILE], int n) {
-                               if (!live) return;
-                               for (int j = 0; j < n; ++j) {
-                                   float x[R];
+        for_each_tile_x<R, TILE>(sm, recA, recB, xr + (size_t)w.real * (size_t)total, total, nr, b, e,
+                                 [&](const uint4* a, const float4* bb, const float (*xs)[R], int n) {
+                                     if (!live) return;
+                                     for (int j = 0; j < n; ++j) {
+                                         float x[R];
+                                         if constexpr (R == 4) {
+                                             const float4 v = *reinterpret_cast<const float4*>(xs[j]);
+                                             x[0] = v.x;
+                                             x[1] = v.y;
+                                             x[2] = v.z;
+                                             x[3] = v.w;
+                                         } else {
 #pragma unroll
-                                   for (int r = 0; r < R; ++r) x[r] = xs[r][j];
-                                   st.add(a[j], bb[j], x, k0);
-                               }
-                           });
+                                             for (int r = 0; r < R; ++r) x[r] = xs[j][r];
+                                         }
+                                         st.add(a[j], bb[j], x, k0);
+                                     }
+                                 });
         const float n = (float)(e - b);
 #pragma unroll
         for (int r = 0; r < R; ++r) {

@@ -329,6 +329,42 @@ struct MStrip {
     }
 };
 
+// One 128-bit shared-memory load of a 16-byte record.  A float4 whose fourth
+// word goes unused is split by the compiler into narrower loads: one more
+// instruction per sample.
+__device__ __forceinline__ uint4 lds128(const void* p) {
+    uint4 r;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "r"(a)
+                 : "memory");
+    return r;
+}
+
+// The samples of one staged tile through a strip, x from the records: each
+// record pair with two 128-bit loads, and full tiles (n == TILE) with a
+// constant trip count.  Measured with one-warp CTAs: 1.3% faster for the
+// single-curve kernel, 14% for the batch kernel (76.6 -> 65.9 ms on the
+// 4096-curve Monte Carlo), than float4 loads in a loop over n.
+template <int TILE, class S>
+__device__ __forceinline__ void strip_tile(S& st, const uint4* a, const float4* b, int n, uint32_t k0) {
+    auto sample = [&](int j) {
+        const uint4 A = lds128(a + j);
+        const uint4 Bu = lds128(b + j);
+        const float4 B = make_float4(__uint_as_float(Bu.x), __uint_as_float(Bu.y), __uint_as_float(Bu.z),
+                                     __uint_as_float(Bu.w));
+        st.add(A, B, B.x, k0);
+    };
+    if (n == TILE) {
+#pragma unroll 2
+        for (int j = 0; j < TILE; ++j) sample(j);
+    } else {
+#pragma unroll 2
+        for (int j = 0; j < n; ++j) sample(j);
+    }
+}
+
 // Double-buffered cp.async pipeline over the samples [j0, j1) in tiles of
 // TILE samples (kTile unless a kernel is built for another tile length):
 // stages the two 16-byte phase records of every sample and, when `xr` is

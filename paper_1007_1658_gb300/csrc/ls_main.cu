@@ -65,20 +65,6 @@ __device__ __forceinline__ void write_out(const float (&xc)[F], const float (&xs
     }
 }
 
-// One 128-bit shared-memory load of a 16-byte record (the compiler splits
-// a float4 whose fourth word goes unused into narrower loads: one more
-// instruction per sample; measured 1.3% faster on the 100k x 200k workload
-// together with the constant trip count of full tiles).
-__device__ __forceinline__ uint4 lds128(const void* p) {
-    uint4 r;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "r"(a)
-                 : "memory");
-    return r;
-}
-
 template <int F, int MODE>
 __global__ void __launch_bounds__(kMainThreads)
 ls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, int64_t N, int64_t chunk,
@@ -90,23 +76,9 @@ ls_main_kernel(const uint4* __restrict__ recA, const float4* __restrict__ recB, 
     Strip<F, MODE> st;
     st.zero();
     const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
-    auto sample = [&](const uint4* a, const float4* b, int j) {
-        const uint4 A = lds128(a + j);
-        const uint4 Bu = lds128(b + j);
-        const float4 B = make_float4(__uint_as_float(Bu.x), __uint_as_float(Bu.y), __uint_as_float(Bu.z),
-                                     __uint_as_float(Bu.w));
-        st.add(A, B, B.x, k0);
-    };
     for_each_tile<false>(sm, recA, recB, nullptr, j0, j1,
                          [&](const uint4* a, const float4* b, const float*, int n) {
-                             if (!live) return;
-                             if (n == kTile) {  // full tiles: a constant trip count
-#pragma unroll 2
-                                 for (int j = 0; j < kTile; ++j) sample(a, b, j);
-                             } else {
-#pragma unroll 2
-                                 for (int j = 0; j < n; ++j) sample(a, b, j);
-                             }
+                             if (live) strip_tile<kTile>(st, a, b, n, k0);
                          });
     float xc[F], xs[F], cc[F], cs[F];
 #pragma unroll

@@ -138,3 +138,27 @@ def test_tuning_file_of_another_gpu_is_not_applied(lsp, tmp_path):
     assert e.value.status == lsp.ERR_INVALID_ARG
     ctx.close()
     ctx2.close()
+
+
+def test_single_curve_tuning_round_trip(lsp, tmp_path):
+    """lsp_autotune's entry survives lsp_tune_save / lsp_tune_load, and a fresh
+    context that loaded it still matches the oracle on a curve of that bucket."""
+    from paper_1007_1658_gb300 import synth
+    c = synth.plain_1k()
+    ctx = lsp.Context(0)
+    chosen = ctx.autotune(c.t.size, c.nf)
+    path = tmp_path / "tune1.json"
+    ctx.tune_save(path)
+    doc, _ = _batch_entries(path)
+    single = [e for e in doc["entries"] if e["kind"] == 1]
+    assert len(single) == 1
+    e = single[0]
+    assert (e["sincos"], e["F"]) == (chosen["sincos_mode"], chosen["freqs_per_thread"])
+    ctx2 = lsp.Context(0)
+    assert ctx2.tune_load(path) == 1
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    P = ctx2.periodogram(d(c.t), d(c.X), c.f0, c.df, c.nf)
+    ctx2.sync(60.0)
+    assert_parity(P.cpu().numpy(), oracle.periodogram(c.t, c.X, c.f0, c.df, c.nf), what="loaded tuning entry")
+    ctx.close()
+    ctx2.close()
