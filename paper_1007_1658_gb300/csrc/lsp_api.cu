@@ -98,9 +98,19 @@ MainShape lsp::host::choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
 }
 
 // Frequency blocks, padding and the N_t split of a shape whose mode and F are
-// set; occ = resident CTAs per SM of its kernel.
+// set; occ = resident CTAs per SM of its kernel, `threads` its CTA size,
+// `ops` its FMA-pipe operations per term and `rows` its partial sums per
+// frequency.  The automatic split minimizes a time model: the CTAs of equal
+// work run in waves of occ x SMs, so the main kernel takes about
+// ceil(CTAs / slots) x chunk sample-steps, each costing (ops F + 16) issue
+// slots for every warp sharing a sub-partition; the partial sums of the
+// chunks are written and read back once (at ~4 TB/s).  Chunks stay within
+// kMaxChunk samples (precision) and above kMinChunk.  On the 100k x 200k
+// periodogram this picks 65 chunks over 7 waves (main kernel 3.74 ms) where
+// filling a single wave as fully as possible took 9 chunks (3.88 ms: 2,349 of
+// 2,432 slots busy).
 void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64_t N, int64_t N_f, int split,
-                             int threads) {
+                             int threads, int ops, int rows) {
     const int64_t per_block = (int64_t)threads * s.F;
     s.nfb = (int)((N_f + per_block - 1) / per_block);
     s.nf_pad = (int64_t)s.nfb * per_block;
@@ -111,17 +121,19 @@ void lsp::host::finish_shape(const lsp_ctx* ctx, MainShape& s, int occ_in, int64
         // at most kMaxChunk samples per chunk, then up to 255 more splits
         const int64_t lo = std::min<int64_t>(65535, std::max<int64_t>(1, (N + lsp::kMaxChunk - 1) / lsp::kMaxChunk));
         const int64_t hi = std::min<int64_t>(65535, std::max<int64_t>(lo, std::min<int64_t>(max_split, lo + 255)));
-        double best = -1.0;
+        const double warps_per_subpartition = std::max(1.0, (double)occ * (threads / 32) / 4.0);
+        const double step_s = (ops * s.F + 16.0) * warps_per_subpartition / (0.9 * 2.0e9);
+        const double part_bytes_per_split = (double)s.nf_pad * rows * 4.0 * 2.0;  // written, then read
+        double best = 1e300;
         int64_t best_s = lo;
         for (int64_t sp = lo; sp <= hi; ++sp) {
             const int64_t ctas = (int64_t)s.nfb * sp;
             const int64_t waves = (ctas + slots - 1) / slots;
-            // fraction of SM slots busy over the run, slightly favouring fewer
-            // splits (a relative penalty, so a grid far below one wave still
-            // takes every split it can)
-            const double eff = (double)ctas / (double)(waves * slots) / (1.0 + 0.002 * (double)(sp - lo));
-            if (eff > best + 1e-9) {
-                best = eff;
+            const int64_t chunk = (N + sp - 1) / sp;
+            const double t = (double)waves * (double)chunk * step_s +
+                             (sp > 1 ? (double)sp * part_bytes_per_split / 4.0e12 : 0.0);
+            if (t < best * (1.0 - 1e-3)) {  // a new split must win by 0.1%
+                best = t;
                 best_s = sp;
             }
         }

@@ -285,10 +285,12 @@ void default_mode_F(const lsp_options& o, int* mode, int* F);
 // Launch shape of the single-curve path for the context's options.
 lsp::MainShape choose_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f);
 
-// Frequency blocks, padding and N_t split (split <= 0: fill whole waves of
-// occ resident CTAs per SM) of a shape whose mode and F are already set.
+// Frequency blocks, padding and N_t split (split <= 0: the split that a model
+// of waves x chunk length plus partial-sum traffic rates fastest) of a shape
+// whose mode and F are already set; occ resident CTAs of `threads` per SM,
+// `ops` FMA-pipe operations per term, `rows` partial sums per frequency.
 void finish_shape(const lsp_ctx* ctx, lsp::MainShape& s, int occ, int64_t N, int64_t N_f, int split,
-                  int threads = lsp::kMainThreads);
+                  int threads = lsp::kMainThreads, int ops = 6, int rows = 4);
 
 // Autotuned entry for this size bucket, or null.
 const TuneEntry* tuned(const lsp_ctx* ctx, int64_t N, int64_t N_f);

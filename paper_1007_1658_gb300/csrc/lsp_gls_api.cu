@@ -34,7 +34,7 @@ MainShape choose_gls_shape(const lsp_ctx* ctx, int64_t N, int64_t N_f) {
         s.F = 16;
     }
     if (o.freqs_per_thread == 8 || o.freqs_per_thread == 12 || o.freqs_per_thread == 16) s.F = o.freqs_per_thread;
-    finish_shape(ctx, s, lsp::gls_occupancy(s.mode, s.F), N, N_f, o.split, lsp::kGlsThreads);
+    finish_shape(ctx, s, lsp::gls_occupancy(s.mode, s.F), N, N_f, o.split, lsp::kGlsThreads, 8, lsp::kGlsRows);
     return s;
 }
 
