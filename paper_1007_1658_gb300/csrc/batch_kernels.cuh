@@ -66,13 +66,13 @@ __device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, in
         // the single-curve kernel's loop: x from the records
         constexpr int T = sizeof(sm.A[0]) / sizeof(uint4);  // the tile length of this kernel
         for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
-            if (live) strip_tile<T>(st, a, bb, n, k0);
+            if (live) strip_tile<T, false>(st, a, bb, n, k0);
         });
     } else {
         for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
             if (!live) return;
 #pragma unroll 2
-            for (int j = 0; j < n; ++j) st.add(a[j], bb[j], xs[j], k0);
+            for (int j = 0; j < n; ++j) st.template add<false>(a[j], bb[j], xs[j], k0);
         });
     }
     const float n = (float)(e - b);

@@ -58,7 +58,7 @@ struct GStrip {
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
         uint32_t p = top_phase_hi(A, k0);
         if (MODE == kMufu) {
-            const uint32_t du = __float_as_uint(B.w);
+            const uint32_t du = round_top_word(A);
 #pragma unroll
             for (int i = 0; i < F; ++i) {
                 float s, c;
@@ -67,7 +67,7 @@ struct GStrip {
                 p += du;
             }
         } else {
-            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            const float C = B.y, S = B.z, C2 = B.w;
             float s, c;
             __sincosf(phase_to_angle(p), &s, &c);
             c *= q;
@@ -122,7 +122,7 @@ struct GStrip<F, kRecur3x2> {
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
         const uint32_t p = top_phase_hi(A, k0);
-        const float C = B.y, S = B.z, C2 = 2.f * B.y;
+        const float C = B.y, S = B.z, C2 = B.w;
         float s, c;
         __sincosf(phase_to_angle(p), &s, &c);
         c *= q;
@@ -236,18 +236,18 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
 }
 
 // Many curves in one persistent launch: CTAs take (curve, block of
-// kGlsThreads*F frequencies) items from an atomic ticket, run the strip over
+// kGlsBatchThreads*F frequencies) items from an atomic ticket, run the strip over
 // all samples of the curve, finish p in FP64, write P if asked and fold the
 // block's largest P into the curve's (P bits << 32 | ~k) maximum.
 template <int F, int MODE>
-__global__ void __launch_bounds__(kGlsThreads)
+__global__ void __launch_bounds__(kGlsBatchThreads)
 gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
                  const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
                  const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
                  const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey) {
-    __shared__ __align__(16) TileSmemN<1, kGlsTile> sm;
+    __shared__ __align__(16) TileSmemN<1, kGlsBatchTile> sm;
     __shared__ int s_item;
-    __shared__ unsigned long long s_red[kGlsThreads / 32];
+    __shared__ unsigned long long s_red[kGlsBatchThreads / 32];
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
         __syncthreads();
@@ -257,12 +257,12 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         const BatchItem w = items[it];
         const int64_t b = off[w.curve], e = off[w.curve + 1];
         const int64_t N_f = nf[w.curve];
-        const uint32_t k0 = (uint32_t)w.fblock * (kGlsThreads * F) + (uint32_t)threadIdx.x * F;
+        const uint32_t k0 = (uint32_t)w.fblock * (kGlsBatchThreads * F) + (uint32_t)threadIdx.x * F;
         GStrip<F, MODE> st;
         st.zero();
         const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
         for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e,
-                           [&](const uint4* a, const float4* bb, const float (*qs)[kGlsTile], int n) {
+                           [&](const uint4* a, const float4* bb, const float (*qs)[kGlsBatchTile], int n) {
                                if (!live) return;
 #pragma unroll 2
                                for (int j = 0; j < n; ++j) {
@@ -286,7 +286,7 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long m = s_red[0];
-            for (int x = 1; x < kGlsThreads / 32; ++x) m = umax64(m, s_red[x]);
+            for (int x = 1; x < kGlsBatchThreads / 32; ++x) m = umax64(m, s_red[x]);
             if (m) atomicMax(&maxkey[w.curve], m);
         }
     }
@@ -366,7 +366,7 @@ int gls_batch_occupancy(int mode, int F) {
     const GlsBatchFn fn = gls_batch_fn(mode, F);
     if (!fn) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsThreads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsBatchThreads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -379,7 +379,7 @@ cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, 
                              cudaStream_t st) {
     const GlsBatchFn fn = gls_batch_fn(mode, F);
     if (!fn) return cudaErrorInvalidValue;
-    fn<<<grid, kGlsThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
+    fn<<<grid, kGlsBatchThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,10 @@ __device__ __forceinline__ uint32_t top_phase_hi(const uint4& A, uint32_t k) {
     return __umulhi(k, A.x) + k * A.y + A.w;
 }
 
+// round(u / 2^32) of record A: the phase step of one frequency bin in the
+// 32-bit turns that top_phase returns (the MUFU strips add it per bin).
+__device__ __forceinline__ uint32_t round_top_word(const uint4& A) { return A.y + (A.x >> 31); }
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -153,11 +157,14 @@ struct Strip {
     }
 
     // Sample with phase record A = {u, v}, B = {x_hat, cos 2 pi u, sin 2 pi u,
-    // round(u / 2^32)} and normalized value x.
+    // 2 cos 2 pi u} and normalized value x.  C2_REC takes the recurrence factor
+    // from the record, else it is formed as 2 B.y (the same value): which is
+    // faster depends on the kernel around the strip, so each kernel picks.
+    template <bool C2_REC = true>
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, uint32_t k0) {
         uint32_t p = top_phase(A, k0);
         if (MODE == kMufu) {
-            const uint32_t du = __float_as_uint(B.w);
+            const uint32_t du = round_top_word(A);
 #pragma unroll
             for (int i = 0; i < F; ++i) {
                 float s, c;
@@ -170,7 +177,7 @@ struct Strip {
             // (cos, sin)(2 pi u): RECUR uses the angle-addition formulas at
             // every step; RECUR3 uses them once and then the three-term form
             // z_{i+1} = 2 cos(2 pi u) z_i - z_{i-1}.
-            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            const float C = B.y, S = B.z, C2 = C2_REC ? B.w : 2.f * B.y;
             float s, c;
             __sincosf(phase_to_angle(p), &s, &c);
             float cp = c, sp = s;
@@ -234,8 +241,9 @@ struct Strip<F, kRecur3x2> {
         cs2[i] = __ffma2_rn(yc, ys, cs2[i]);
     }
 
+    template <bool C2_REC = true>
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, uint32_t k0) {
-        const float C = B.y, S = B.z, C2 = 2.f * B.y;
+        const float C = B.y, S = B.z, C2 = C2_REC ? B.w : 2.f * B.y;
         float sa, ca, sb, cb;
         __sincosf(phase_to_angle(top_phase(A, k0)), &sa, &ca);
         __sincosf(phase_to_angle(top_phase(A, k0 + H)), &sb, &cb);
@@ -294,7 +302,7 @@ struct MStrip {
     __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], uint32_t k0) {
         uint32_t p = top_phase(A, k0);
         if (MODE == kMufu) {
-            const uint32_t du = __float_as_uint(B.w);
+            const uint32_t du = round_top_word(A);
 #pragma unroll
             for (int i = 0; i < F; ++i) {
                 float s, c;
@@ -303,7 +311,7 @@ struct MStrip {
                 p += du;
             }
         } else {
-            const float C = B.y, S = B.z, C2 = 2.f * B.y;
+            const float C = B.y, S = B.z, C2 = B.w;
             float s, c;
             __sincosf(phase_to_angle(p), &s, &c);
             float cp = c, sp = s;
@@ -347,14 +355,14 @@ __device__ __forceinline__ uint4 lds128(const void* p) {
 // constant trip count.  Measured with one-warp CTAs: 1.3% faster for the
 // single-curve kernel, 14% for the batch kernel (76.6 -> 65.9 ms on the
 // 4096-curve Monte Carlo), than float4 loads in a loop over n.
-template <int TILE, class S>
+template <int TILE, bool C2_REC = true, class S>
 __device__ __forceinline__ void strip_tile(S& st, const uint4* a, const float4* b, int n, uint32_t k0) {
     auto sample = [&](int j) {
         const uint4 A = lds128(a + j);
         const uint4 Bu = lds128(b + j);
         const float4 B = make_float4(__uint_as_float(Bu.x), __uint_as_float(Bu.y), __uint_as_float(Bu.z),
                                      __uint_as_float(Bu.w));
-        st.add(A, B, B.x, k0);
+        st.template add<C2_REC>(A, B, B.x, k0);
     };
     if (n == TILE) {
 #pragma unroll 2

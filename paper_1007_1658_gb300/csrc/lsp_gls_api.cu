@@ -200,7 +200,7 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     // mode and strip length as for the single-curve floating-mean call
     const MainShape shape = choose_gls_shape(ctx, 1 << 20, 1 << 24);
     const int mode = shape.mode, F = shape.F;
-    const int64_t per_block = lsp::gls_freqs_per_block(F);
+    const int64_t per_block = lsp::gls_batch_freqs_per_block(F);
     std::vector<int> order(n_curves);
     for (int c = 0; c < n_curves; ++c) order[c] = c;
     std::stable_sort(order.begin(), order.end(),

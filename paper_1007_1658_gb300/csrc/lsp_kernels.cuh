@@ -26,7 +26,8 @@ struct CurveStats {
 // Phase records of one sample, 32 bytes, consumed by the main kernels.
 //   A = {u_lo, u_hi, v_lo, v_hi}: u = frac(t' df), v = frac(t' f0) + offsets,
 //       both as 64-bit fixed-point turns (t' = t - t_ref).
-//   B = {x_hat, cos 2 pi u, sin 2 pi u, bits of round(u / 2^32)}.
+//   B = {x_hat, cos 2 pi u, sin 2 pi u, 2 cos 2 pi u}; the last one is the factor
+//       of the three-term recurrence, stored so the strips need not form it.
 // The offsets folded into v: 2^63 (half a turn, so that the bit-trick angle
 // below lands on the true phase), 2^31 (round the top word) and 2^40 (round
 // the 23-bit mantissa taken from the top word).
@@ -94,6 +95,9 @@ constexpr int kTile = 128;
 // tiles, which measured 4.5% faster for them than one-warp CTAs.
 constexpr int kGlsThreads = 128;
 constexpr int kGlsTile = 256;
+// CTA shape of the persistent floating-mean batch kernel.
+constexpr int kGlsBatchThreads = 32;
+constexpr int kGlsBatchTile = 128;
 // Fewest samples per N_t chunk that the launch-shape heuristic makes.  A
 // problem too small to fill one wave of CTAs is latency-bound: each thread's
 // serial loop over its chunk is the critical path, so such problems are split
@@ -111,6 +115,7 @@ constexpr int64_t kMaxChunk = int64_t(1) << 14;
 // Frequencies covered by one CTA of the main kernel (of a floating-mean kernel).
 inline int freqs_per_block(int F) { return kMainThreads * F; }
 inline int gls_freqs_per_block(int F) { return kGlsThreads * F; }
+inline int gls_batch_freqs_per_block(int F) { return kGlsBatchThreads * F; }
 
 // Resident CTAs per SM of the main kernel for (mode, F).
 int main_occupancy(int mode, int F);

@@ -243,7 +243,6 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
         const double tt = t[j] - st.t_ref;
         const uint64_t u = frac_turns64(tt, df);
         const uint64_t v = frac_turns64(tt, f0) + kPhaseOffset;
-        const uint32_t du = (uint32_t)((u + (1ull << 31)) >> 32);
         // rotation of one grid step, cos/sin(2 pi u), from the exact fixed-point turn
         float sn, cs;
         rotation_of(u, &cs, &sn);
@@ -263,7 +262,7 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
             if (status) atomicOr(status, kStatusPhaseRange);
         }
         recA[j] = make_uint4((uint32_t)u, (uint32_t)(u >> 32), (uint32_t)v, (uint32_t)(v >> 32));
-        recB[j] = make_float4(xh, cs, sn, __uint_as_float(du));
+        recB[j] = make_float4(xh, cs, sn, 2.f * cs);
         if (recN) recN[j] = make_float2(xh, __double2float_rn(tt));
         if (xout) xout[j] = xh;
     }
