@@ -213,9 +213,11 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 4)
  * share each pass over a curve's samples: the phase, the sin/cos recurrence
  * and CC, CS are computed once for the group and only XC, XS per realization
- * (strips of 16, 12, 4 frequencies for R = 2, 4, 8), which halves the
- * arithmetic per periodogram; each (frequency, realization) is computed
- * exactly as the one-at-a-time kernel with the same strip length would.
+ * (strips of 16, 12, 8 frequencies for R = 2, 4, 8), which halves the
+ * arithmetic per periodogram.  With n_real >= 3 R, CC and CS (which depend on
+ * the sampling pattern only) come from one extra pass per curve instead of
+ * from every group.  Each (frequency, realization) is computed exactly as the
+ * one-at-a-time kernel with the same strip length would.
  * A work item sums over all samples of its curve in FP32 (the batch does not
  * split N_t), so curves far beyond 10^6 samples are better served by
  * lsp_periodogram, which bounds each running sum to 16,384 samples.

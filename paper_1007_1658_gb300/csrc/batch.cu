@@ -26,17 +26,18 @@ BatchFn batch_fn(int mode, int F, bool xrec, int tailF, int tile) {
     }
 }
 
-BatchFn mrhs_fn(int mode, int F, int R, int tile) {
+MrhsFn mrhs_fn(int mode, int F, int R, int tile, bool win) {
     switch (mode) {
         case kModeRecur3:
-        case kModeRecur3x2: return mrhs_fn_recur3(F, R, tile);  // shared-recurrence strips use the scalar form
+        case kModeRecur3x2: return mrhs_fn_recur3(F, R, tile, win);  // shared-recurrence strips use the scalar form
         case kModeMufu:
-        case kModeRecur: return tile == kTile ? mrhs_fn_other(mode, F, R) : nullptr;
+        case kModeRecur: return tile == kTile ? mrhs_fn_other(mode, F, R, win) : nullptr;
         default: return nullptr;
     }
 }
 
-int occupancy_of(BatchFn fn) {
+template <class Fn>
+int occupancy_of(Fn fn) {
     if (!fn) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kMainThreads, 0) != cudaSuccess) {
@@ -50,16 +51,30 @@ int occupancy_of(BatchFn fn) {
 
 int batch_default_tail(int F) { return F > kBatchTailF ? kBatchTailF : 0; }
 
-int mrhs_occupancy(int mode, int F, int R, int tile) { return occupancy_of(mrhs_fn(mode, F, R, tile)); }
+int mrhs_occupancy(int mode, int F, int R, int tile, bool win) {
+    return occupancy_of(mrhs_fn(mode, F, R, tile, win));
+}
 
 cudaError_t launch_mrhs(int mode, int F, int R, int tile, int grid, const BatchItem* items, int n_items,
                         unsigned* head, const int64_t* off, const int64_t* nf, int64_t total, int n_curves,
                         const uint4* recA, const float4* recB, const float* xr, float* P_out, const int64_t* P_off,
-                        int64_t P_total, unsigned long long* maxkey, cudaStream_t st) {
-    BatchFn fn = mrhs_fn(mode, F, R, tile);
-    if (!fn) return cudaErrorInvalidValue;
+                        int64_t P_total, unsigned long long* maxkey, const float2* win, const int64_t* woff,
+                        cudaStream_t st) {
+    MrhsFn fn = mrhs_fn(mode, F, R, tile, win != nullptr);
+    if (!fn || (win && !woff)) return cudaErrorInvalidValue;
     fn<<<grid, kMainThreads, 0, st>>>(items, n_items, head, off, nf, total, n_curves, recA, recB, xr, P_out, P_off,
-                                      P_total, maxkey);
+                                      P_total, maxkey, win, woff);
+    return cudaGetLastError();
+}
+
+int window_occupancy(int mode, int F) { return occupancy_of(window_fn(mode, F)); }
+
+cudaError_t launch_window(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+                          const int64_t* off, const int64_t* nf, const int64_t* woff, const uint4* recA,
+                          const float4* recB, float2* win, cudaStream_t st) {
+    WindowFn fn = window_fn(mode, F);
+    if (!fn) return cudaErrorInvalidValue;
+    fn<<<grid, kMainThreads, 0, st>>>(items, n_items, head, off, nf, woff, recA, recB, win);
     return cudaGetLastError();
 }
 

@@ -2,23 +2,26 @@
 #include "batch_kernels.cuh"
 
 namespace lsp {
+namespace {
 
-BatchFn mrhs_fn_other(int mode, int F, int R) {
+template <int MODE, bool WIN>
+MrhsFn pick_other(int F, int R) {
     using namespace dev;
-    if (mode == kMufu) {
-        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kMufu, kTile>;
-        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kMufu, kTile>;
-        if (F == 8 && R == 2) return ls_mrhs_kernel<8, 2, kMufu, kTile>;
-        if (F == 16 && R == 2) return ls_mrhs_kernel<16, 2, kMufu, kTile>;
-        if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, kMufu, kTile>;
-    }
-    if (mode == kRecur) {
-        if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, kRecur, kTile>;
-        if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, kRecur, kTile>;
-        if (F == 8 && R == 2) return ls_mrhs_kernel<8, 2, kRecur, kTile>;
-        if (F == 16 && R == 2) return ls_mrhs_kernel<16, 2, kRecur, kTile>;
-        if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, kRecur, kTile>;
-    }
+    if (F == 8 && R == 4) return ls_mrhs_kernel<8, 4, MODE, kTile, WIN>;
+    if (F == 12 && R == 4) return ls_mrhs_kernel<12, 4, MODE, kTile, WIN>;
+    if (F == 8 && R == 2) return ls_mrhs_kernel<8, 2, MODE, kTile, WIN>;
+    if (F == 16 && R == 2) return ls_mrhs_kernel<16, 2, MODE, kTile, WIN>;
+    if (F == 4 && R == 8) return ls_mrhs_kernel<4, 8, MODE, kTile, WIN>;
+    if (F == 8 && R == 8) return ls_mrhs_kernel<8, 8, MODE, kTile, WIN>;
+    return nullptr;
+}
+
+}  // namespace
+
+MrhsFn mrhs_fn_other(int mode, int F, int R, bool win) {
+    using namespace dev;
+    if (mode == kMufu) return win ? pick_other<kMufu, true>(F, R) : pick_other<kMufu, false>(F, R);
+    if (mode == kRecur) return win ? pick_other<kRecur, true>(F, R) : pick_other<kRecur, false>(F, R);
     return nullptr;
 }
 

@@ -34,11 +34,22 @@ BatchFn batch_fn_mufu(int F, bool xrec);
 BatchFn batch_fn_recur(int F, bool xrec);
 BatchFn batch_fn_recur3(int F, bool xrec, int tailF, int tile);
 BatchFn batch_fn_recur3x2(int F, bool xrec);
-// Multi-realization shapes (F, R) in {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)},
+// Multi-realization kernels take two more arguments: the window sums (CC, CS)
+// of every frequency of every curve, curve c's at win[woff[c] + k], which the
+// kernels built with win = true read instead of accumulating (the others
+// ignore both).
+using MrhsFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, int64_t, int,
+                        const uint4*, const float4*, const float*, float*, const int64_t*, int64_t,
+                        unsigned long long*, const float2*, const int64_t*);
+// Multi-realization shapes (F, R) in {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8), (8, 8)},
 // tiles of kTile; the three-term recurrence at (12, 4) and (8, 4) also with
-// tiles of 256 and 512.
-BatchFn mrhs_fn_recur3(int F, int R, int tile);
-BatchFn mrhs_fn_other(int mode, int F, int R);
+// tiles of 256 and 512; each with and without the window sums from WStrip.
+MrhsFn mrhs_fn_recur3(int F, int R, int tile, bool win);
+MrhsFn mrhs_fn_other(int mode, int F, int R, bool win);
+// The window pass (ls_window_kernel) for the strip lengths above.
+using WindowFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const int64_t*,
+                          const uint4*, const float4*, float2*);
+WindowFn window_fn(int mode, int F);
 
 namespace {
 
@@ -196,13 +207,14 @@ __device__ __forceinline__ void for_each_tile_x(TileSmemX<R, TILE>& sm, const ui
     }
 }
 
-template <int F, int R, int MODE, int TILE>
+template <int F, int R, int MODE, int TILE, bool WIN>
 __global__ void __launch_bounds__(kMainThreads)
 ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
                const int64_t* __restrict__ off, const int64_t* __restrict__ nf, int64_t total, int n_curves,
                const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ xr,
                float* __restrict__ P_out, const int64_t* __restrict__ P_off, int64_t P_total,
-               unsigned long long* __restrict__ maxkey) {
+               unsigned long long* __restrict__ maxkey, const float2* __restrict__ win,
+               const int64_t* __restrict__ woff) {
     __shared__ __align__(16) TileSmemX<R, TILE> sm;
     __shared__ int s_item;
     __shared__ unsigned long long s_red[R][kMainThreads / 32];
@@ -217,7 +229,7 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
         const int64_t N_f = nf[w.curve];
         const int nr = w.pad;
         const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
-        MStrip<F, R, MODE> st;
+        MStrip<F, R, MODE, !WIN> st;
         st.zero();
         const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
         for_each_tile_x<R, TILE>(sm, recA, recB, xr + (size_t)w.real * (size_t)total, total, nr, b, e,
@@ -225,12 +237,15 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
                                      if (!live) return;
                                      for (int j = 0; j < n; ++j) {
                                          float x[R];
-                                         if constexpr (R == 4) {
-                                             const float4 v = *reinterpret_cast<const float4*>(xs[j]);
-                                             x[0] = v.x;
-                                             x[1] = v.y;
-                                             x[2] = v.z;
-                                             x[3] = v.w;
+                                         if constexpr (R % 4 == 0) {  // R/4 128-bit loads
+#pragma unroll
+                                             for (int q = 0; q < R / 4; ++q) {
+                                                 const float4 v = reinterpret_cast<const float4*>(xs[j])[q];
+                                                 x[4 * q] = v.x;
+                                                 x[4 * q + 1] = v.y;
+                                                 x[4 * q + 2] = v.z;
+                                                 x[4 * q + 3] = v.w;
+                                             }
                                          } else {
 #pragma unroll
                                              for (int r = 0; r < R; ++r) x[r] = xs[j][r];
@@ -239,6 +254,7 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
                                      }
                                  });
         const float n = (float)(e - b);
+        const float2* wc = WIN ? win + woff[w.curve] : nullptr;  // the pattern's window sums
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             unsigned long long best = 0ull;
@@ -247,7 +263,16 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
             for (int i = 0; i < F; ++i) {
                 const uint32_t k = k0 + i;
                 if (k < (uint32_t)N_f && r < nr) {
-                    const float p = periodogram_value(st.xc[i][r], st.xs[i][r], st.cc[i], st.cs[i], n);
+                    float cc_k, cs_k;
+                    if constexpr (WIN) {
+                        const float2 w2 = wc[k];
+                        cc_k = w2.x;
+                        cs_k = w2.y;
+                    } else {
+                        cc_k = st.cc[i];
+                        cs_k = st.cs[i];
+                    }
+                    const float p = periodogram_value(st.xc[i][r], st.xs[i][r], cc_k, cs_k, n);
                     if (P) P[k] = p;
                     best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
                 }
@@ -262,6 +287,44 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
             for (int q = 1; q < kMainThreads / 32; ++q) m = umax64(m, s_red[r][q]);
             if (m) atomicMax(&maxkey[(size_t)(w.real + r) * n_curves + w.curve], m);
         }
+    }
+}
+
+// Window pass: CC and CS of Eq. 8 at every frequency of every curve, win[woff[c] + k]
+// = (CC, CS), by the strips of F frequencies that the multi-realization kernel of
+// the same F uses (k0 a multiple of F), so its groups read the sums they would have
+// accumulated, bit for bit.  Persistent over (curve, block of kMainThreads F
+// frequencies) items like the batch kernels.
+template <int F, int MODE>
+__global__ void __launch_bounds__(kMainThreads)
+ls_window_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
+                 const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const int64_t* __restrict__ woff,
+                 const uint4* __restrict__ recA, const float4* __restrict__ recB, float2* __restrict__ win) {
+    __shared__ __align__(16) TileSmem<false> sm;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const int64_t b = off[w.curve], e = off[w.curve + 1];
+        const int64_t N_f = nf[w.curve];
+        const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
+        WStrip<F, MODE> st;
+        st.zero();
+        const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
+        for_each_tile<false>(sm, recA, recB, nullptr, b, e,
+                             [&](const uint4* a, const float4* bb, const float*, int n) {
+                                 if (!live) return;
+#pragma unroll 2
+                                 for (int j = 0; j < n; ++j) st.add(a[j], bb[j], k0);
+                             });
+        float2* out = win + woff[w.curve];
+#pragma unroll
+        for (int i = 0; i < F; ++i)
+            if (k0 + i < (uint32_t)N_f) out[k0 + i] = make_float2(st.cc[i], st.cs[i]);
     }
 }
 

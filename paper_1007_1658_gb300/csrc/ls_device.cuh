@@ -276,7 +276,10 @@ struct Strip<F, kRecur3x2> {
 // XC, XS.  Per term and realization: 2 FFMA plus (2 recurrence + 2 CC/CS)/R,
 // instead of 6.  The arithmetic of every (frequency, realization) pair is the
 // single-realization strip's, in the same order, so results are identical.
-template <int F, int R, int MODE>
+// With CCS false the strip leaves CC and CS out (they depend on the sampling
+// pattern only, and WStrip computes them once for all groups): 2 + 2/R per
+// term and realization, and 2F fewer registers.
+template <int F, int R, int MODE, bool CCS = true>
 struct MStrip {
     float xc[F][R], xs[F][R], cc[F], cs[F];
 
@@ -295,8 +298,10 @@ struct MStrip {
             xc[i][r] = fmaf(x[r], c, xc[i][r]);
             xs[i][r] = fmaf(x[r], s, xs[i][r]);
         }
-        cc[i] = fmaf(c, c, cc[i]);
-        cs[i] = fmaf(c, s, cs[i]);
+        if (CCS) {
+            cc[i] = fmaf(c, c, cc[i]);
+            cs[i] = fmaf(c, s, cs[i]);
+        }
     }
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], uint32_t k0) {
@@ -318,6 +323,63 @@ struct MStrip {
 #pragma unroll
             for (int i = 0; i < F; ++i) {
                 acc(i, x, c, s);
+                if (i + 1 < F) {
+                    float cn, sn;
+                    if (MODE == kRecur || i == 0) {
+                        cn = fmaf(c, C, -s * S);
+                        sn = fmaf(s, C, c * S);
+                    } else {
+                        cn = fmaf(C2, c, -cp);
+                        sn = fmaf(C2, s, -sp);
+                    }
+                    cp = c;
+                    sp = s;
+                    c = cn;
+                    s = sn;
+                }
+            }
+        }
+    }
+};
+
+// The window sums CC = sum cos^2 and CS = sum cos sin of Eq. 8 alone, for a
+// strip of F frequencies: the same seed, step and order as MStrip (and Strip)
+// of the same F and k0, so the sums are bit for bit theirs.  They do not
+// depend on the data, so one pass per sampling pattern serves every group of
+// realizations of that pattern.
+template <int F, int MODE>
+struct WStrip {
+    float cc[F], cs[F];
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) cc[i] = cs[i] = 0.f;
+    }
+
+    __device__ __forceinline__ void acc(int i, float c, float s) {
+        cc[i] = fmaf(c, c, cc[i]);
+        cs[i] = fmaf(c, s, cs[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, uint32_t k0) {
+        uint32_t p = top_phase(A, k0);
+        if (MODE == kMufu) {
+            const uint32_t du = round_top_word(A);
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                float s, c;
+                __sincosf(phase_to_angle(p), &s, &c);
+                acc(i, c, s);
+                p += du;
+            }
+        } else {
+            const float C = B.y, S = B.z, C2 = B.w;
+            float s, c;
+            __sincosf(phase_to_angle(p), &s, &c);
+            float cp = c, sp = s;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                acc(i, c, s);
                 if (i + 1 < F) {
                     float cn, sn;
                     if (MODE == kRecur || i == 0) {

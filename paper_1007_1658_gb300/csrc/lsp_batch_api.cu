@@ -77,9 +77,10 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
         if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
     }
     // strip lengths measured best on GB300 for each group size (256 patterns x 64 realizations)
-    int F = R == 1 ? F1 : (R == 8 ? 4 : (R == 4 ? 12 : 16));
+    int F = R == 1 ? F1 : (R == 8 ? 8 : (R == 4 ? 12 : 16));
     // multi-realization strips: a strip length asked for replaces the default when that shape exists
-    if (R > 1 && ctx->opt.freqs_per_thread && lsp::mrhs_occupancy(mode, ctx->opt.freqs_per_thread, R, lsp::kTile) > 0)
+    if (R > 1 && ctx->opt.freqs_per_thread &&
+        lsp::mrhs_occupancy(mode, ctx->opt.freqs_per_thread, R, lsp::kTile, false) > 0)
         F = ctx->opt.freqs_per_thread;
     int tailF = lsp::batch_default_tail(F), tile = lsp::kTile;
     // a shape from lsp_autotune_batch for batches like this one, when the
@@ -98,13 +99,18 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
         tailF = shape->tailF;
         tile = shape->tile;
         if (R != shape->R) {  // fewer realizations than the tuned group: the default shape of this group
-            F = R == 1 ? 24 : (R == 8 ? 4 : (R == 4 ? 12 : 16));
+            F = R == 1 ? 24 : (R == 8 ? 8 : (R == 4 ? 12 : 16));
             tailF = lsp::batch_default_tail(F);
             tile = lsp::kTile;
         }
     }
     const bool xrec = n_real == 1;  // x travels inside the sample records
-    if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0)
+    // with three groups of realizations or more per pattern, CC and CS come from
+    // one window pass per pattern (4 FMA-pipe ops per term) instead of from every
+    // group (2 per term and group), which also frees 2F registers per thread
+    const bool use_win = R > 1 && n_real >= 3 * R;
+    if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile, use_win) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0 ||
+        (use_win && lsp::window_occupancy(mode, F) <= 0))
         return fail(ctx, LSP_ERR_UNSUPPORTED, "batch shape (mode %d, F %d, R %d, tail %d, tile %d) is not built", mode,
                     F, R, tailF, tile);
     const int64_t per_block = lsp::freqs_per_block(F);
@@ -136,6 +142,10 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     if (!p_dev && (rs = ensure(ctx, ctx->b_P, (size_t)n_real * (size_t)P_total * 4)) != LSP_OK) return rs;
     if (!m_dev && (rs = ensure(ctx, ctx->b_maxP, n_out * 4)) != LSP_OK) return rs;
     if (!a_dev && (rs = ensure(ctx, ctx->b_argmax, n_out * 4)) != LSP_OK) return rs;
+    if (use_win) {
+        if ((rs = ensure(ctx, ctx->b_win, (size_t)nf_total * 8)) != LSP_OK) return rs;
+        if ((rs = ensure(ctx, ctx->b_woff, ((size_t)n_curves + 1) * 8)) != LSP_OK) return rs;
+    }
     float* d_P = P_out ? (p_dev ? P_out : (float*)ctx->b_P.p) : nullptr;
     float* d_maxP = maxP_out ? (m_dev ? maxP_out : (float*)ctx->b_maxP.p) : nullptr;
     int32_t* d_argmax = argmax_out ? (a_dev ? argmax_out : (int32_t*)ctx->b_argmax.p) : nullptr;
@@ -143,7 +153,9 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     // ---- plan: reuse the cached graph when nothing it depends on changed ----
     const std::vector<const void*> ptrs = {d_off, d_nf, d_f0, d_df, d_poff, d_t, d_X, d_P, d_maxP, d_argmax,
                                            ctx->b_recA.p, ctx->b_recB.p, ctx->b_xr.p, ctx->b_stats.p,
-                                           ctx->b_head.p, ctx->b_seed.p, ctx->b_maxkey.p, ctx->b_items.p};
+                                           ctx->b_head.p, ctx->b_seed.p, ctx->b_maxkey.p,
+                                           use_win ? ctx->b_win.p : nullptr, use_win ? ctx->b_woff.p : nullptr,
+                                           ctx->b_items.p};
     BatchPlan& pl = ctx->plan;
     const bool same = pl.valid && pl.n_curves == n_curves && pl.n_real == n_real && pl.mode == mode &&
                       pl.F == F && pl.R == R && pl.tailF == tailF && pl.tile == tile && pl.noise == noise &&
@@ -172,21 +184,42 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
                     for (int r = 0; r < n_real; ++r) items.push_back({c, r, (int32_t)nfb, (int32_t)(-1 - tb)});
             }
         }
+        // window pass: one item per (curve, block of strips of F), after the main items
+        const size_t n_main = items.size();
+        std::vector<int64_t> woff;
+        if (use_win) {
+            woff.assign((size_t)n_curves + 1, 0);
+            for (int c = 0; c < n_curves; ++c) woff[c + 1] = woff[c] + nf[c];
+            for (int c : order)
+                for (int64_t fb = 0; fb < (nf[c] + per_block - 1) / per_block; ++fb) items.push_back({c, 0, (int32_t)fb, 0});
+        }
+        const size_t n_win = items.size() - n_main;
         if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
         const size_t item_bytes = items.size() * sizeof(lsp::BatchItem);
+        const size_t woff_bytes = woff.size() * sizeof(int64_t);
         const void* old_items = ctx->b_items.p;
         if ((rs = ensure(ctx, ctx->b_items, item_bytes + 16)) != LSP_OK) return rs;
-        if ((rs = ensure_pinned(ctx, item_bytes + 64)) != LSP_OK) return rs;
+        if ((rs = ensure_pinned(ctx, item_bytes + woff_bytes + 64)) != LSP_OK) return rs;
         LSP_CUDA(ctx, cudaStreamSynchronize(st));  // the pinned buffer may still feed an earlier copy
         if (!items.empty()) {
             std::memcpy(ctx->pinned, items.data(), item_bytes);
             LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_items.p, ctx->pinned, item_bytes, cudaMemcpyHostToDevice, st));
         }
+        if (use_win) {
+            char* hw = (char*)ctx->pinned + ((item_bytes + 15) & ~(size_t)15);
+            std::memcpy(hw, woff.data(), woff_bytes);
+            LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_woff.p, hw, woff_bytes, cudaMemcpyHostToDevice, st));
+        }
         std::vector<const void*> ptrs2 = ptrs;
         ptrs2.back() = ctx->b_items.p;
         (void)old_items;
-        const int occ = R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile) : lsp::batch_occupancy(mode, F, xrec, tailF, tile);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
+        const int occ =
+            R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile, use_win) : lsp::batch_occupancy(mode, F, xrec, tailF, tile);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)n_main));
+        const int grid_w = use_win ? (int)std::max<int64_t>(
+                                         1, std::min<int64_t>((int64_t)lsp::window_occupancy(mode, F) * ctx->sms,
+                                                              (int64_t)n_win))
+                                   : 0;
 
         // capture the batch as one graph, on a private stream (the caller's
         // stream may be the legacy default stream, which cannot be captured);
@@ -211,12 +244,19 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
         if (e == cudaSuccess && noise)
             e = lsp::launch_noise_prep(d_off, n_curves, n_real, (const uint64_t*)ctx->b_seed.p, total,
                                        (float*)ctx->b_xr.p, (float4*)ctx->b_recB.p, cst);
-        if (e == cudaSuccess && !items.empty() && R > 1)
-            e = lsp::launch_mrhs(mode, F, R, tile, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)items.size(),
+        if (e == cudaSuccess && n_win > 0)
+            e = lsp::launch_window(mode, F, grid_w, (const lsp::BatchItem*)ctx->b_items.p + n_main, (int)n_win,
+                                   (unsigned*)ctx->b_head.p + 1, d_off, d_nf, (const int64_t*)ctx->b_woff.p,
+                                   (const uint4*)ctx->b_recA.p, (const float4*)ctx->b_recB.p,
+                                   (float2*)ctx->b_win.p, cst);
+        if (e == cudaSuccess && n_main > 0 && R > 1)
+            e = lsp::launch_mrhs(mode, F, R, tile, grid, (const lsp::BatchItem*)ctx->b_items.p, (int)n_main,
                                  (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves, (const uint4*)ctx->b_recA.p,
                                  (const float4*)ctx->b_recB.p, (const float*)ctx->b_xr.p, d_P, d_poff, P_total,
-                                 (unsigned long long*)ctx->b_maxkey.p, cst);
-        else if (e == cudaSuccess && !items.empty())
+                                 (unsigned long long*)ctx->b_maxkey.p,
+                                 use_win ? (const float2*)ctx->b_win.p : nullptr,
+                                 use_win ? (const int64_t*)ctx->b_woff.p : nullptr, cst);
+        else if (e == cudaSuccess && n_main > 0)
             e = lsp::launch_batch(mode, F, xrec, tailF, tile, grid, (const lsp::BatchItem*)ctx->b_items.p,
                                   (int)items.size(),
                                   (unsigned*)ctx->b_head.p, d_off, d_nf, total, n_curves,
@@ -250,9 +290,9 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
         pl.f0 = f0v;
         pl.df = dfv;
         pl.p_off = poff;
-        pl.n_items = (int)items.size();
+        pl.n_items = (int)n_main;
         pl.grid = grid;
-        pl.kernels = 3 + (noise ? 1 : 0) + ((d_maxP || d_argmax) ? 1 : 0) + (items.empty() ? -1 : 0);
+        pl.kernels = 3 + (noise ? 1 : 0) + ((d_maxP || d_argmax) ? 1 : 0) + (n_main == 0 ? -1 : 0) + (n_win > 0 ? 1 : 0);
     }
 
     // ---- run: new seed, one graph launch, outputs back if they live on the host ----

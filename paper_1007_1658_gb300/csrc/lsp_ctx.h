@@ -92,7 +92,8 @@ struct lsp_ctx {
     lsp::host::DevBuf pr_acc, pr_z0, pr_z1;  // Press-Rybicki: FP64 grid, FFT ping-pong buffers
     // batch workspace
     lsp::host::DevBuf b_recA, b_recB, b_xr, b_stats, b_items, b_head, b_maxkey, b_seed, b_off, b_nf, b_f0,
-        b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax;
+        b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax,
+        b_win, b_woff;  // multi-realization window sums (CC, CS) per frequency and their per-curve offsets
     void* pinned = nullptr;  // host staging for the work list and small values
     size_t pinned_cap = 0;
     lsp::host::BatchPlan plan;

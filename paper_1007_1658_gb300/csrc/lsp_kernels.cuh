@@ -189,13 +189,25 @@ cudaError_t launch_batch(int mode, int F, bool x_in_records, int tailF, int tile
 
 // Multi-RHS batch: items carry a group of up to R realizations (real = first,
 // pad = count) sharing phases, recurrence and CC/CS; shapes (F, R) in
-// {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8)} with tiles of kTile, and for the
+// {(8, 4), (12, 4), (8, 2), (16, 2), (4, 8), (8, 8)} with tiles of kTile, and for the
 // three-term recurrence (12, 4) and (8, 4) also with tiles of 256 and 512.
-int mrhs_occupancy(int mode, int F, int R, int tile);
+// With win non-null the kernel takes CC and CS of curve c's frequency k from
+// win[woff[c] + k] (written by launch_window with the same mode and F) instead
+// of accumulating them.
+int mrhs_occupancy(int mode, int F, int R, int tile, bool win);
 cudaError_t launch_mrhs(int mode, int F, int R, int tile, int grid, const BatchItem* items, int n_items,
                         unsigned* head, const int64_t* off, const int64_t* nf, int64_t total, int n_curves,
                         const uint4* recA, const float4* recB, const float* xr, float* P_out, const int64_t* P_off,
-                        int64_t P_total, unsigned long long* maxkey, cudaStream_t st);
+                        int64_t P_total, unsigned long long* maxkey, const float2* win, const int64_t* woff,
+                        cudaStream_t st);
+
+// Window pass of a multi-realization batch: items (curve, block of
+// kMainThreads * F frequencies) from a zeroed ticket counter `head`; writes
+// (CC, CS) of every frequency k < N_f[c] to win[woff[c] + k].  F in {4, 8, 12, 16}.
+int window_occupancy(int mode, int F);
+cudaError_t launch_window(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
+                          const int64_t* off, const int64_t* nf, const int64_t* woff, const uint4* recA,
+                          const float4* recB, float2* win, cudaStream_t st);
 
 cudaError_t launch_unpack_max(const unsigned long long* maxkey, int64_t n, float* maxP, int32_t* argmax,
                               cudaStream_t st);

@@ -239,6 +239,7 @@ extern "C" lsp_status lsp_autotune_batch(lsp_ctx* ctx, int32_t n_curves, const i
         }
         cands.push_back({kModeRecur3, 16, 2, 0, lsp::kTile});
         cands.push_back({kModeRecur3, 4, 8, 0, lsp::kTile});
+        cands.push_back({kModeRecur3, 8, 8, 0, lsp::kTile});
         cands.push_back({kModeRecur3, 24, 1, 8, lsp::kTile});
     }
     const lsp_options saved = ctx->opt;
@@ -250,7 +251,7 @@ extern "C" lsp_status lsp_autotune_batch(lsp_ctx* ctx, int32_t n_curves, const i
     const uint64_t seed = 0x5eed7u;
     for (const BatchShape& sh : cands) {
         if (sh.R > n_real) continue;
-        const int occ = sh.R > 1 ? lsp::mrhs_occupancy(sh.mode, sh.F, sh.R, sh.tile)
+        const int occ = sh.R > 1 ? lsp::mrhs_occupancy(sh.mode, sh.F, sh.R, sh.tile, false)
                                  : lsp::batch_occupancy(sh.mode, sh.F, true, sh.tailF, sh.tile);
         if (occ <= 0) continue;
         float ms = 1e30f;
@@ -352,7 +353,7 @@ extern "C" lsp_status lsp_tune_load(lsp_ctx* ctx, const char* path, int32_t* n_l
                               (int)field(line, "tailF"), (int)field(line, "tile")},
                              (float)field(line, "ms")};
             // only shapes this build has
-            const int occ = e.shape.R > 1 ? lsp::mrhs_occupancy(e.shape.mode, e.shape.F, e.shape.R, e.shape.tile)
+            const int occ = e.shape.R > 1 ? lsp::mrhs_occupancy(e.shape.mode, e.shape.F, e.shape.R, e.shape.tile, false)
                                           : lsp::batch_occupancy(e.shape.mode, e.shape.F, true, e.shape.tailF,
                                                                  e.shape.tile);
             if (occ <= 0) continue;

@@ -63,10 +63,14 @@ def _oracle_noise_curve(b, seed, c, r):
     return t, X
 
 
-@pytest.mark.parametrize("mode", [4, 3, 2, 1])
-def test_noise_batch_matches_oracle(ctx, lsp, mode):
+@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (1, 13)])
+def test_noise_batch_matches_oracle(ctx, lsp, mode, n_real):
+    """Every (curve, realization) periodogram of a noise batch against the
+    oracle on the same Philox noise.  n_real = 3 runs groups of 2 realizations
+    that accumulate their own CC and CS; n_real = 13 runs groups of 4 (the last
+    one partial) that take CC and CS from the window pass."""
     b = _small_batch()
-    seed, n_real = 99, 3
+    seed = 99
     ctx.set_options(sincos_mode=mode)
     P_off = np.zeros(b.n + 1, np.int64)
     P_off[1:] = np.cumsum(b.nf)
@@ -173,20 +177,24 @@ def test_noise_periodograms_follow_the_beta_law(ctx):
     assert stats.kstest(z, stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
 
 
-@pytest.mark.parametrize("R,F", [(2, 8), (2, 16), (4, 8), (4, 12), (8, 4)])
-def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F):
+@pytest.mark.parametrize("groups", [1, 3])
+@pytest.mark.parametrize("R,F", [(2, 8), (2, 16), (4, 8), (4, 12), (8, 4), (8, 8)])
+def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F, groups):
     """Groups of R realizations share the phase, the recurrence and CC/CS; each
     (frequency, realization) must come out bit for bit as the one-at-a-time
     kernel with the same strip length computes it (here with a partial last
-    group).  With strips longer than 8 the one-at-a-time kernel runs the
-    frequencies after a curve's last full block as 8-frequency tail strips, so
-    there the comparison is to FP32 rounding instead."""
+    group).  With one full group per pattern the groups accumulate CC and CS
+    themselves; with three or more they read them from the window pass, which
+    runs strips of the same length.  With strips longer than 8 the
+    one-at-a-time kernel runs the frequencies after a curve's last full block
+    as 8-frequency tail strips, so there the comparison is to FP32 rounding
+    instead."""
     if F <= 8:
         b = _small_batch(n_curves=9, seed=31)
     else:  # curves long enough for several full blocks of the longer strips
         from paper_1007_1658_gb300 import synth
         b = synth.noise_batch(n_curves=6, seed=31, nt_min=1500, nt_max=5000, t_min=5.0, t_max=80.0)
-    n_real = R + R // 2 + 1
+    n_real = groups * R + R // 2 + 1
     P_off = np.zeros(b.n + 1, np.int64)
     P_off[1:] = np.cumsum(b.nf)
     outs = []
@@ -202,7 +210,7 @@ def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F):
         assert np.array_equal(outs[0][0], outs[1][0])
         assert np.array_equal(outs[0][1], outs[1][1]) and np.array_equal(outs[0][2], outs[1][2])
         return
-    block = 128 * F
+    block = 32 * F  # frequencies per block of one-warp CTAs
     for r in range(n_real):
         for c in range(b.n):
             base = r * int(P_off[-1]) + int(P_off[c])
