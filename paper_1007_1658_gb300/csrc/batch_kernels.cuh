@@ -235,7 +235,7 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
         for_each_tile_x<R, TILE>(sm, recA, recB, xr + (size_t)w.real * (size_t)total, total, nr, b, e,
                                  [&](const uint4* a, const float4* bb, const float (*xs)[R], int n) {
                                      if (!live) return;
-                                     for (int j = 0; j < n; ++j) {
+                                     auto sample = [&](int j) {
                                          float x[R];
                                          if constexpr (R % 4 == 0) {  // R/4 128-bit loads
 #pragma unroll
@@ -251,6 +251,15 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
                                              for (int r = 0; r < R; ++r) x[r] = xs[j][r];
                                          }
                                          st.add(a[j], bb[j], x, k0);
+                                     };
+                                     // unrolled twice when the window sums free the registers
+                                     // for it (0.6 % at (12, 4)); with its own CC/CS the
+                                     // strip has no room and measured slower unrolled
+                                     if constexpr (WIN) {
+#pragma unroll 2
+                                         for (int j = 0; j < n; ++j) sample(j);
+                                     } else {
+                                         for (int j = 0; j < n; ++j) sample(j);
                                      }
                                  });
         const float n = (float)(e - b);
