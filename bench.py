@@ -291,7 +291,8 @@ def run_gpu(args, rank, world, dist):
         line["paper_shape"] = _compact(run_paper_shape(torch, dev, stream, args, peaks, sms))
     if args.batch:
         line["multi_rhs"] = _compact(run_mrhs_bench(torch, dev, stream, args.mrhs_patterns, args.mrhs_real,
-                                                    tuple(int(g) for g in args.mrhs_groups.split(","))))
+                                                    tuple(int(g) for g in args.mrhs_groups.split(",")),
+                                                    sms * peaks["sm_max_mhz"] * 1e6))
     if args.probe:
         line["pipe_rates"] = _compact(pipe_rates(ctx, sms, peaks["sm_max_mhz"]))
     if args.cadence:
@@ -573,10 +574,25 @@ def batch_cpu_sample(n_sample=32, seed=1234):
             "kind": "oracle", "sample": "%d random curves of the 4096 (%.3g terms)" % (n_sample, terms)}
 
 
-def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64, groups=(1, 2, 4, 8)):
+def mrhs_ops_per_term(R, n_real):
+    """FMA-pipe operations per term and realization of an lsp_batch call with
+    groups of R realizations: 6 one at a time; else 2 (XC, XS) + 2 recurrence
+    shared by the group, plus CC and CS either in every group (2 / R) or, with
+    three groups or more per pattern, once per pattern in the window pass
+    (4 / n_real)."""
+    if R == 1:
+        return 6.0
+    if n_real >= 3 * R:
+        return 2.0 + 2.0 / R + 4.0 / n_real
+    return 2.0 + 4.0 / R
+
+
+def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64, groups=(1, 2, 4, 8), clk_sm=None):
     """Many realizations per pattern (the surrogate's training shape: 256
     noise_batch patterns x 64 realizations, one lsp_batch call) for each
-    multi-RHS group size; every result is bit-identical across group sizes."""
+    multi-RHS group size; every result is bit-identical across group sizes.
+    With clk_sm (SMs x clock in Hz) each group also gets its FMA-pipe roof
+    (128 lanes/clk/SM over mrhs_ops_per_term) and the fraction reached."""
     from paper_1007_1658_gb300 import lsp, synth
     b = synth.noise_batch(n_curves=n_patterns, seed=777001)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -597,8 +613,13 @@ def run_mrhs_bench(torch, dev, stream, n_patterns=256, n_real=64, groups=(1, 2, 
             mctx.sync(300.0)
         ms = e0.elapsed_time(e1) / 3
         mctx.close()
-        out.append({"batch_rhs": rhs, "ms": ms, "periodograms_per_s": n_real * b.n / (ms * 1e-3),
-                    "terms_per_s": n_real * b.terms / (ms * 1e-3)})
+        row = {"batch_rhs": rhs, "ms": ms, "periodograms_per_s": n_real * b.n / (ms * 1e-3),
+               "terms_per_s": n_real * b.terms / (ms * 1e-3)}
+        if clk_sm:
+            ops = mrhs_ops_per_term(min(rhs, n_real), n_real)
+            row["ops_per_term"] = ops
+            row["frac_of_roof"] = row["terms_per_s"] / (128.0 / ops * clk_sm)
+        out.append(row)
     return {"workload": "%d noise_batch patterns x %d realizations" % (b.n, n_real), "by_group": out}
 
 
