@@ -63,7 +63,7 @@ def _oracle_noise_curve(b, seed, c, r):
     return t, X
 
 
-@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (1, 13)])
+@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (3, 13), (2, 13), (1, 13)])
 def test_noise_batch_matches_oracle(ctx, lsp, mode, n_real):
     """Every (curve, realization) periodogram of a noise batch against the
     oracle on the same Philox noise.  n_real = 3 runs groups of 2 realizations

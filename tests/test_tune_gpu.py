@@ -162,3 +162,43 @@ def test_single_curve_tuning_round_trip(lsp, tmp_path):
     assert_parity(P.cpu().numpy(), oracle.periodogram(c.t, c.X, c.f0, c.df, c.nf), what="loaded tuning entry")
     ctx.close()
     ctx2.close()
+
+
+def test_tuned_multi_realization_shapes_match_the_oracle(lsp):
+    """Multi-realization shapes the tuner may pick, including the tiles of 256
+    and 512 and both group sizes, with 24 realizations (three groups or more,
+    so CC and CS come from the window pass): each agrees with the oracle on
+    the maxima of a few (curve, realization) pairs, and with the others."""
+    b, args = _batch(n=24, seed=717)
+    n_real, seed = 24, 2718
+    refs = {}
+    for c in (0, 9, b.n - 1):
+        for r in (0, 13, n_real - 1):
+            t = b.curve_t(c)
+            refs[c, r] = oracle.periodogram(t, oracle.noise(seed, c, r, t.size), b.f0[c], b.df[c], b.nf[c]).max()
+    base = None
+    path_dir = os.environ.get("TMPDIR", "/tmp")
+    for F, R, tile in ((12, 4, 128), (12, 4, 256), (8, 4, 512), (8, 8, 128), (16, 2, 128)):
+        ctx = lsp.Context(0)
+        ctx.autotune_batch(*args, n_real=n_real)
+        path = os.path.join(path_dir, "lsp_tune_mr_%d_%d_%d_%d.json" % (os.getpid(), F, R, tile))
+        ctx.tune_save(path)
+        doc, entries = _batch_entries(path)
+        entries[0].update(mode=4, F=F, R=R, tailF=0, tile=tile)
+        with open(path, "w") as fh:
+            fh.write('{"lsp_tune": 1, "device": "%s", "entries": [\n' % doc["device"])
+            fh.write(json.dumps(entries[0]) + "\n]}\n")
+        ctx2 = lsp.Context(0)
+        assert ctx2.tune_load(path) == 1
+        os.remove(path)
+        maxP, _ = ctx2.batch(*args, seed=seed, n_real=n_real)
+        ctx2.sync(120.0)
+        assert ctx2.test_last_batch_shape() == (4, F, R, 0, tile)
+        m = maxP.cpu().numpy().astype(np.float64).reshape(n_real, b.n)
+        for (c, r), ref in refs.items():
+            assert abs(m[r, c] - ref) <= 1e-4 * ref, (F, R, tile, c, r)
+        if base is None:
+            base = m
+        assert np.max(np.abs(m - base) / base) <= 2e-5, (F, R, tile)
+        ctx.close()
+        ctx2.close()
