@@ -238,13 +238,15 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
 // Many curves in one persistent launch: CTAs take (curve, block of
 // kGlsBatchThreads*F frequencies) items from an atomic ticket, run the strip over
 // all samples of the curve, finish p in FP64, write P if asked and fold the
-// block's largest P into the curve's (P bits << 32 | ~k) maximum.  Held to 16
-// CTAs (128 registers) per SM: four warps per sub-partition instead of the two
-// that the compiler's free choice (221 registers) leaves; the few values it
-// spills are measured to cost less than the latency the extra warps hide
-// (4096-curve batch 100.9 -> 99.0 ms, results unchanged).
-template <int F, int MODE>
-__global__ void __launch_bounds__(kGlsBatchThreads, 16)
+// block's largest P into the curve's (P bits << 32 | ~k) maximum.  MINB = 16
+// holds the packed strip to 128 registers: four warps per sub-partition
+// instead of the two that the compiler's free choice (221 registers) leaves,
+// for a few spilled values.  That raises throughput (4096-curve batch 100.9 ->
+// 99.0 ms) but halves each warp's own speed, so a batch whose longest curve
+// is a large share of the work (256 curves: 7.2 -> 8.2 ms) runs the unbounded
+// form; results are the same either way.
+template <int F, int MODE, int MINB>
+__global__ void __launch_bounds__(kGlsBatchThreads, MINB)
 gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
                  const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
                  const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
@@ -299,22 +301,23 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
 using GlsBatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const uint4*,
                             const float4*, const float*, float*, const int64_t*, unsigned long long*);
 
-GlsBatchFn gls_batch_fn(int mode, int F) {
+GlsBatchFn gls_batch_fn(int mode, int F, bool packed) {
+    if (packed) return F == 16 && mode == kRecur3x2 ? gls_batch_kernel<16, kRecur3x2, 16> : nullptr;
     if (F == 16) {
         switch (mode) {
-            case kMufu: return gls_batch_kernel<16, kMufu>;
-            case kRecur: return gls_batch_kernel<16, kRecur>;
-            case kRecur3: return gls_batch_kernel<16, kRecur3>;
-            case kRecur3x2: return gls_batch_kernel<16, kRecur3x2>;
+            case kMufu: return gls_batch_kernel<16, kMufu, 1>;
+            case kRecur: return gls_batch_kernel<16, kRecur, 1>;
+            case kRecur3: return gls_batch_kernel<16, kRecur3, 1>;
+            case kRecur3x2: return gls_batch_kernel<16, kRecur3x2, 1>;
             default: return nullptr;
         }
     }
     if (F == 8) {
         switch (mode) {
-            case kMufu: return gls_batch_kernel<8, kMufu>;
-            case kRecur: return gls_batch_kernel<8, kRecur>;
-            case kRecur3: return gls_batch_kernel<8, kRecur3>;
-            case kRecur3x2: return gls_batch_kernel<8, kRecur3x2>;
+            case kMufu: return gls_batch_kernel<8, kMufu, 1>;
+            case kRecur: return gls_batch_kernel<8, kRecur, 1>;
+            case kRecur3: return gls_batch_kernel<8, kRecur3, 1>;
+            case kRecur3x2: return gls_batch_kernel<8, kRecur3x2, 1>;
             default: return nullptr;
         }
     }
@@ -366,8 +369,8 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
     return cudaGetLastError();
 }
 
-int gls_batch_occupancy(int mode, int F) {
-    const GlsBatchFn fn = gls_batch_fn(mode, F);
+int gls_batch_occupancy(int mode, int F, bool packed) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F, packed);
     if (!fn) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsBatchThreads, 0) != cudaSuccess) {
@@ -377,11 +380,11 @@ int gls_batch_occupancy(int mode, int F) {
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
-                             const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
-                             const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
-                             cudaStream_t st) {
-    const GlsBatchFn fn = gls_batch_fn(mode, F);
+cudaError_t launch_gls_batch(int mode, int F, bool packed, int grid, const BatchItem* items, int n_items,
+                             unsigned* head, const int64_t* off, const int64_t* nf, const uint4* recA,
+                             const float4* recB, const float* q, float* P_out, const int64_t* P_off,
+                             unsigned long long* maxkey, cudaStream_t st) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F, packed);
     if (!fn) return cudaErrorInvalidValue;
     fn<<<grid, kGlsBatchThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
     return cudaGetLastError();

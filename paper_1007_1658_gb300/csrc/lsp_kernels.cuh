@@ -139,11 +139,13 @@ cudaError_t launch_gls_finalize(const MainShape& s, const float* part, int64_t N
                                 cudaStream_t st);
 struct BatchItem;
 // Many curves (CSR samples, per-curve grids) in one persistent launch; F in {8, 16}.
-int gls_batch_occupancy(int mode, int F);
-cudaError_t launch_gls_batch(int mode, int F, int grid, const BatchItem* items, int n_items, unsigned* head,
-                             const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
-                             const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
-                             cudaStream_t st);
+// packed: the form held to 16 CTAs per SM (built for F = 16, RECUR3 x2), for
+// batches whose work is many times their longest curve's.
+int gls_batch_occupancy(int mode, int F, bool packed = false);
+cudaError_t launch_gls_batch(int mode, int F, bool packed, int grid, const BatchItem* items, int n_items,
+                             unsigned* head, const int64_t* off, const int64_t* nf, const uint4* recA,
+                             const float4* recB, const float* q, float* P_out, const int64_t* P_off,
+                             unsigned long long* maxkey, cudaStream_t st);
 
 // ---- Press-Rybicki fast approximation (press_rybicki.cu) ----
 
