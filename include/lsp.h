@@ -61,9 +61,10 @@ typedef enum lsp_sincos_mode {
                               fewer instructions per term: the classic kernels put
                               the two halves of each strip in the two lanes (results
                               bit-identical to RECUR3 with strips of half the length),
-                              the floating-mean kernels the (cos, sin) pair
-                              (bit-identical to RECUR3 at the same length); the
-                              multi-realization batch kernels use the scalar form    */
+                              the floating-mean kernels and the multi-realization
+                              groups that read the window pass the (cos, sin) pair
+                              (bit-identical to RECUR3 at the same length); other
+                              multi-realization groups use the scalar form         */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */
@@ -210,14 +211,16 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  * maxP_out, argmax_out (optional, [n_real * n_curves], index r * n_curves + c):
  *   the largest P of each periodogram and its bin k (lowest k on ties; -1 and
  *   0 for a curve with N_f = 0).
- * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 4)
- * share each pass over a curve's samples: the phase, the sin/cos recurrence
- * and CC, CS are computed once for the group and only XC, XS per realization
- * (strips of 16, 12, 8 frequencies for R = 2, 4, 8), which halves the
- * arithmetic per periodogram.  With n_real >= 3 R, CC and CS (which depend on
- * the sampling pattern only) come from one extra pass per curve instead of
- * from every group.  Each (frequency, realization) is computed exactly as the
- * one-at-a-time kernel with the same strip length would.
+ * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 8
+ * when n_real >= 24, else 4) share each pass over a curve's samples: the
+ * phase, the sin/cos recurrence and CC, CS are computed once for the group
+ * and only XC, XS per realization (strips of 16, 12, 8 frequencies for
+ * R = 2, 4, 8), which halves the arithmetic per periodogram.  With
+ * n_real >= 3 R, CC and CS (which depend on the sampling pattern only) come
+ * from one extra pass per curve instead of from every group, and under the
+ * AUTO sin/cos mode the groups then run the packed strip (RECUR3_X2).  Each
+ * (frequency, realization) is computed exactly as the one-at-a-time kernel
+ * with the same strip length would.
  * A work item sums over all samples of its curve in FP32 (the batch does not
  * split N_t), so curves far beyond 10^6 samples are better served by
  * lsp_periodogram, which bounds each running sum to 16,384 samples.

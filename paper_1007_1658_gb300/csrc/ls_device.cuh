@@ -292,6 +292,9 @@ struct MStrip {
         }
     }
 
+    __device__ __forceinline__ float get_xc(int i, int r) const { return xc[i][r]; }
+    __device__ __forceinline__ float get_xs(int i, int r) const { return xs[i][r]; }
+
     __device__ __forceinline__ void acc(int i, const float (&x)[R], float c, float s) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -338,6 +341,59 @@ struct MStrip {
                     s = sn;
                 }
             }
+        }
+    }
+};
+
+// Packed form of the multi-realization strip without CC and CS (the window
+// sums come from WStrip): the (cos, sin) pair of a frequency sits in the two
+// lanes of an FFMA2, so (XC, XS) of one realization take one FFMA2 per term
+// and the three-term step one FFMA2 for both lanes; per term and realization
+// the FMA pipe does the same 2 + 2/R lane operations in half the issue slots.
+// FFMA2 has no negated addend, so the lanes carry y_i = g_i z_i with the signs
+// g = (+, +, -, -, +, +, ...) of the other packed strips, and the running sums
+// are kept as g_i (XC, XS): g_i is the same for every sample, and round to
+// nearest is symmetric, so g_i times the sums is bit for bit
+// MStrip<F, R, kRecur3, false>'s XC and XS.
+template <int F, int R>
+struct MStrip<F, R, kRecur3x2, false> {
+    float2 a[F][R];  // g_i (XC, XS) of frequency i, realization r
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i)
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[i][r] = make_float2(0.f, 0.f);
+    }
+
+    __device__ __forceinline__ float get_xc(int i, int r) const { return ((i >> 1) & 1) ? -a[i][r].x : a[i][r].x; }
+    __device__ __forceinline__ float get_xs(int i, int r) const { return ((i >> 1) & 1) ? -a[i][r].y : a[i][r].y; }
+
+    __device__ __forceinline__ void acc(int i, const float2 (&xp)[R], float2 y) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[i][r] = __ffma2_rn(xp[r], y, a[i][r]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], uint32_t k0) {
+        const float C = B.y, S = B.z, C2 = B.w;
+        float s, c;
+        __sincosf(phase_to_angle(top_phase(A, k0)), &s, &c);
+        float2 xp[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) xp[r] = make_float2(x[r], x[r]);
+        float2 y0 = make_float2(c, s);
+        acc(0, xp, y0);
+        if (F == 1) return;
+        // first step by angle addition, as the scalar strip takes it
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, xp, y1);
+        const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
+#pragma unroll
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            acc(i, xp, y2);
+            y0 = y1;
+            y1 = y2;
         }
     }
 };

@@ -71,9 +71,11 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     if (mode == lsp::kModeNaive)
         return fail(ctx, LSP_ERR_UNSUPPORTED, "lsp_batch does not offer the naive FP32 phase");
     // realizations per pass over the samples (multi-RHS) and the strip length that goes with it
+    // (auto: 8 when that makes three groups or more, so that the window pass
+    // and the packed strips serve them; else 4)
     int R = 1;
     if (n_real > 1) {
-        R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : 4;
+        R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : (n_real >= 24 ? 8 : 4);
         if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
     }
     // strip lengths measured best on GB300 for each group size (256 patterns x 64 realizations)
@@ -109,6 +111,11 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     // one window pass per pattern (4 FMA-pipe ops per term) instead of from every
     // group (2 per term and group), which also frees 2F registers per thread
     const bool use_win = R > 1 && n_real >= 3 * R;
+    // groups that take CC and CS from the window pass run the packed strip
+    // (bit-identical to the scalar one; 256 patterns x 64 realizations at R = 8:
+    // 131.4 -> 104.2 ms), unless the options or a tuned shape chose the form
+    if (use_win && !shape && ctx->opt.sincos_mode == LSP_SINCOS_AUTO && mode == lsp::kModeRecur3)
+        mode = lsp::kModeRecur3x2;
     if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile, use_win) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0 ||
         (use_win && lsp::window_occupancy(mode, F) <= 0))
         return fail(ctx, LSP_ERR_UNSUPPORTED, "batch shape (mode %d, F %d, R %d, tail %d, tile %d) is not built", mode,

@@ -63,12 +63,15 @@ def _oracle_noise_curve(b, seed, c, r):
     return t, X
 
 
-@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (3, 13), (2, 13), (1, 13)])
+@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (3, 13), (2, 13), (1, 13),
+                                         (0, 13), (0, 27)])
 def test_noise_batch_matches_oracle(ctx, lsp, mode, n_real):
     """Every (curve, realization) periodogram of a noise batch against the
     oracle on the same Philox noise.  n_real = 3 runs groups of 2 realizations
     that accumulate their own CC and CS; n_real = 13 runs groups of 4 (the last
-    one partial) that take CC and CS from the window pass."""
+    one partial) that take CC and CS from the window pass, in the packed strip
+    under the automatic and packed modes; n_real = 27 runs the automatic
+    groups of 8 (packed, the last group partial)."""
     b = _small_batch()
     seed = 99
     ctx.set_options(sincos_mode=mode)
@@ -177,18 +180,20 @@ def test_noise_periodograms_follow_the_beta_law(ctx):
     assert stats.kstest(z, stats.beta(1, (N - 3) / 2).cdf).pvalue > 1e-3
 
 
+@pytest.mark.parametrize("packed", [False, True])
 @pytest.mark.parametrize("groups", [1, 3])
 @pytest.mark.parametrize("R,F", [(2, 8), (2, 16), (4, 8), (4, 12), (8, 4), (8, 8)])
-def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F, groups):
+def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F, groups, packed):
     """Groups of R realizations share the phase, the recurrence and CC/CS; each
     (frequency, realization) must come out bit for bit as the one-at-a-time
     kernel with the same strip length computes it (here with a partial last
     group).  With one full group per pattern the groups accumulate CC and CS
     themselves; with three or more they read them from the window pass, which
-    runs strips of the same length.  With strips longer than 8 the
-    one-at-a-time kernel runs the frequencies after a curve's last full block
-    as 8-frequency tail strips, so there the comparison is to FP32 rounding
-    instead."""
+    runs strips of the same length, and in the packed mode run the packed
+    strip (the (cos, sin) pair in the two FFMA2 lanes, signs folded into the
+    sums).  With strips longer than 8 the one-at-a-time kernel runs the
+    frequencies after a curve's last full block as 8-frequency tail strips, so
+    there the comparison is to FP32 rounding instead."""
     if F <= 8:
         b = _small_batch(n_curves=9, seed=31)
     else:  # curves long enough for several full blocks of the longer strips
@@ -199,7 +204,8 @@ def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F, groups):
     P_off[1:] = np.cumsum(b.nf)
     outs = []
     for rhs in (1, R):
-        ctx = lsp.Context(0, sincos_mode=3, freqs_per_thread=F, batch_rhs=rhs)
+        mode = 4 if packed and rhs > 1 else 3
+        ctx = lsp.Context(0, sincos_mode=mode, freqs_per_thread=F, batch_rhs=rhs)
         P = np.empty(n_real * int(P_off[-1]), np.float32)
         mx = np.empty(n_real * b.n, np.float32)
         am = np.empty(n_real * b.n, np.int32)

@@ -40,7 +40,7 @@ def _batch_entries(path):
     return doc, [e for e in doc["entries"] if e["kind"] == 2]
 
 
-@pytest.mark.parametrize("n_real", [1, 8])
+@pytest.mark.parametrize("n_real", [1, 8, 30])
 def test_tuned_batch_uses_its_shape_and_matches_the_oracle(lsp, tmp_path, n_real):
     b, args = _batch()
     ctx = lsp.Context(0)
@@ -51,6 +51,8 @@ def test_tuned_batch_uses_its_shape_and_matches_the_oracle(lsp, tmp_path, n_real
     assert len(entries) == 1
     e = entries[0]
     assert chosen["freqs_per_thread"] == e["F"] and chosen["batch_rhs"] == e["R"]
+    # internal kernel mode -> public sin/cos mode: recurrence, three-term, packed three-term
+    assert chosen["sincos_mode"] == {2: 2, 4: 3, 5: 4}[e["mode"]]
     seed = 4321
     maxP, argmax = ctx.batch(*args, seed=seed, n_real=n_real)
     ctx.sync(120.0)
@@ -166,9 +168,10 @@ def test_single_curve_tuning_round_trip(lsp, tmp_path):
 
 def test_tuned_multi_realization_shapes_match_the_oracle(lsp):
     """Multi-realization shapes the tuner may pick, including the tiles of 256
-    and 512 and both group sizes, with 24 realizations (three groups or more,
-    so CC and CS come from the window pass): each agrees with the oracle on
-    the maxima of a few (curve, realization) pairs, and with the others."""
+    and 512, every group size and the packed strips (internal mode 5), with 24
+    realizations (three groups or more, so CC and CS come from the window
+    pass): each agrees with the oracle on the maxima of a few (curve,
+    realization) pairs, and with the others."""
     b, args = _batch(n=24, seed=717)
     n_real, seed = 24, 2718
     refs = {}
@@ -178,13 +181,14 @@ def test_tuned_multi_realization_shapes_match_the_oracle(lsp):
             refs[c, r] = oracle.periodogram(t, oracle.noise(seed, c, r, t.size), b.f0[c], b.df[c], b.nf[c]).max()
     base = None
     path_dir = os.environ.get("TMPDIR", "/tmp")
-    for F, R, tile in ((12, 4, 128), (12, 4, 256), (8, 4, 512), (8, 8, 128), (16, 2, 128)):
+    for mode, F, R, tile in ((4, 12, 4, 128), (4, 12, 4, 256), (4, 8, 4, 512), (4, 8, 8, 128), (4, 16, 2, 128),
+                             (5, 12, 4, 128), (5, 8, 8, 128), (5, 16, 2, 128)):
         ctx = lsp.Context(0)
         ctx.autotune_batch(*args, n_real=n_real)
         path = os.path.join(path_dir, "lsp_tune_mr_%d_%d_%d_%d.json" % (os.getpid(), F, R, tile))
         ctx.tune_save(path)
         doc, entries = _batch_entries(path)
-        entries[0].update(mode=4, F=F, R=R, tailF=0, tile=tile)
+        entries[0].update(mode=mode, F=F, R=R, tailF=0, tile=tile)
         with open(path, "w") as fh:
             fh.write('{"lsp_tune": 1, "device": "%s", "entries": [\n' % doc["device"])
             fh.write(json.dumps(entries[0]) + "\n]}\n")
@@ -193,12 +197,12 @@ def test_tuned_multi_realization_shapes_match_the_oracle(lsp):
         os.remove(path)
         maxP, _ = ctx2.batch(*args, seed=seed, n_real=n_real)
         ctx2.sync(120.0)
-        assert ctx2.test_last_batch_shape() == (4, F, R, 0, tile)
+        assert ctx2.test_last_batch_shape() == (mode, F, R, 0, tile)
         m = maxP.cpu().numpy().astype(np.float64).reshape(n_real, b.n)
         for (c, r), ref in refs.items():
-            assert abs(m[r, c] - ref) <= 1e-4 * ref, (F, R, tile, c, r)
+            assert abs(m[r, c] - ref) <= 1e-4 * ref, (mode, F, R, tile, c, r)
         if base is None:
             base = m
-        assert np.max(np.abs(m - base) / base) <= 2e-5, (F, R, tile)
+        assert np.max(np.abs(m - base) / base) <= 2e-5, (mode, F, R, tile)
         ctx.close()
         ctx2.close()
