@@ -368,7 +368,7 @@ const char *lsp_last_error(const lsp_ctx *ctx);
 #define LSP_FAP_LEVELS 9
 
 /*
- * Features of n sampling patterns (CSR t_off/t, sorted times, 2..32769
+ * Features of n sampling patterns (CSR t_off/t, sorted times, 2 .. 2^31 - 1
  * samples each; grid f_0 >= 0, df > 0, N_f >= 1 as for lsp_batch) into
  * features[n][32] (FP32).  With T = t_last - t_first, dt the M = N - 1 gaps,
  * q(p) = sorted(dt)[floor(p (M - 1))], med = q(1/2), f_max = f_0 + (N_f-1) df:

@@ -11,10 +11,13 @@
 //                        on f_m = m df, m = 1..floor(f_max / df): the same
 //                        persistent tile loop as the batch periodogram, x = 1;
 //   features_kernel   -- one CTA per pattern: cadence order statistics (a
-//                        bitonic sort of the gaps in shared memory), gap
+//                        bitonic sort of the gaps in shared memory, or for
+//                        patterns of more than 32,768 gaps a radix select of
+//                        the five ranks over the gaps in global memory), gap
 //                        fractions, and the 8 highest window maxima outside
 //                        the main lobe (per-thread top-8 lists merged by
 //                        warp shuffles).
+#include <algorithm>
 #include <cfloat>
 
 #include "ls_device.cuh"
@@ -25,6 +28,63 @@ namespace {
 using namespace dev;
 
 constexpr int kFeatThreads = 1024;
+constexpr int kSortMaxGaps = 32768;  // gaps sorted in shared memory (128 KB); more are selected
+
+// The five cadence order statistics sorted(gaps)[k[i]] of a pattern too long
+// for the shared-memory sort, without sorting: an MSB-first radix select on
+// the FP32 bit patterns of the gaps (ordered as the values, gaps being >= 0),
+// 8 bits per pass and the five ranks at once, the gaps re-formed from t in
+// every pass exactly as the sort forms them.  Each warp adds to the five
+// 256-bin histograms once per distinct bin (__match_any_sync), so gaps that
+// share their leading bits do not serialize on one counter.  hist holds
+// 5 x 256 counters; out[i] receives the value of rank k[i].
+__device__ void select_gap_ranks(const double* __restrict__ t, int64_t b, int M, const int (&k)[5],
+                                 unsigned* hist, float* out) {
+    __shared__ unsigned s_prefix[5], s_rank[5];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    if (tid < 5) {
+        s_prefix[tid] = 0u;
+        s_rank[tid] = (unsigned)k[tid];
+    }
+    unsigned mask = 0u;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 5 * 256; i += nt) hist[i] = 0u;
+        __syncthreads();
+        unsigned prefix[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) prefix[q] = s_prefix[q];
+        // the whole warp steps together so that every lane takes part in the match
+        for (int base = tid - lane; base < M; base += nt) {
+            const int i = base + lane;
+            unsigned key = 0u;
+            if (i < M) key = __float_as_uint((float)(t[b + i + 1] - t[b + i]));
+            const int bin = (int)((key >> shift) & 255u);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const int mine = (i < M && (key & mask) == prefix[q]) ? bin : -1;
+                const unsigned peers = __match_any_sync(0xffffffffu, mine);
+                if (mine >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[q * 256 + mine], (unsigned)__popc(peers));
+            }
+        }
+        __syncthreads();
+        if (tid < 5) {
+            // the bin holding rank s_rank: ranks below it move to the next pass's count
+            unsigned r = s_rank[tid], acc = 0u;
+            int bin = 0;
+            for (; bin < 255; ++bin) {
+                const unsigned c = hist[tid * 256 + bin];
+                if (acc + c > r) break;
+                acc += c;
+            }
+            s_rank[tid] = r - acc;
+            s_prefix[tid] |= (unsigned)bin << shift;
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    if (tid < 5) out[tid] = __uint_as_float(s_prefix[tid]);
+    __syncthreads();
+}
 
 template <int F>
 __global__ void __launch_bounds__(kMainThreads)
@@ -76,7 +136,8 @@ __device__ __forceinline__ void top8_insert(float (&v)[8], int (&m)[8], float x,
     m[p] = mi;
 }
 
-// One CTA per pattern.  Dynamic shared memory: the gaps, padded to a power of two.
+// One CTA per pattern.  Dynamic shared memory: the gaps, padded to a power of
+// two, for patterns of up to kSortMaxGaps gaps; the select's histograms for longer ones.
 __global__ void __launch_bounds__(kFeatThreads)
 features_kernel(const double* __restrict__ t, const int64_t* __restrict__ off, const double* __restrict__ f0a,
                 const double* __restrict__ dfa, const int64_t* __restrict__ nfa, const float* __restrict__ W,
@@ -87,16 +148,27 @@ features_kernel(const double* __restrict__ t, const int64_t* __restrict__ off, c
     __shared__ float wv[32 * 8];
     __shared__ int wm[32 * 8];
     __shared__ int unsorted;
+    __shared__ float qsel[5];
     const int c = blockIdx.x;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t b = off[c], e = off[c + 1];
     const int n = (int)(e - b), M = n - 1;
+    const double ps[5] = {0.05, 0.25, 0.5, 0.75, 0.95};
     int P2 = 1;
     while (P2 < M) P2 <<= 1;
+    const bool sorted_in_smem = M <= kSortMaxGaps;
     if (tid == 0) unsorted = 0;
     __syncthreads();
     const double T = t[e - 1] - t[b];
-    for (int i = tid; i < P2; i += nt) {
+    if (!sorted_in_smem) {
+        int k[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) k[i] = (int)floor(ps[i] * (double)(M - 1));
+        select_gap_ranks(t, b, M, k, (unsigned*)gaps, qsel);
+        for (int i = tid; i < M; i += nt)
+            if (t[b + i + 1] - t[b + i] < 0.0) unsorted = 1;
+    }
+    for (int i = tid; sorted_in_smem && i < P2; i += nt) {
         if (i < M) {
             const double d = t[b + i + 1] - t[b + i];
             if (d < 0.0) unsorted = 1;
@@ -107,7 +179,7 @@ features_kernel(const double* __restrict__ t, const int64_t* __restrict__ off, c
     }
     __syncthreads();
     // bitonic sort, ascending
-    for (int k = 2; k <= P2; k <<= 1) {
+    for (int k = 2; sorted_in_smem && k <= P2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             for (int i = tid; i < P2; i += nt) {
                 const int l = i ^ j;
@@ -123,8 +195,9 @@ features_kernel(const double* __restrict__ t, const int64_t* __restrict__ off, c
             __syncthreads();
         }
     }
-    auto q = [&](double p) { return gaps[(int)floor(p * (double)(M - 1))]; };
-    const double med = (double)gaps[(M - 1) / 2];
+    // q(ps[i]) = sorted(gaps)[floor(ps[i] (M - 1))]; the median is q(1/2)
+    auto q = [&](int i) { return sorted_in_smem ? gaps[(int)floor(ps[i] * (double)(M - 1))] : qsel[i]; };
+    const double med = (double)q(2);
     // gap sums over dt > c med (1 + 1e-6): the margin keeps exact multiples of
     // the cadence (one dropped sample on an even grid) out of the gaps
     double s2 = 0.0, s10 = 0.0, s100 = 0.0, cnt2 = 0.0, mx = 0.0;
@@ -233,8 +306,7 @@ features_kernel(const double* __restrict__ t, const int64_t* __restrict__ off, c
         o[3] = (float)log(1.0 / (df * T));
         o[4] = (float)log(f_max * T / (double)n);
         o[5] = (float)log1p(f0 / df);
-        const double ps[5] = {0.05, 0.25, 0.5, 0.75, 0.95};
-        for (int i = 0; i < 5; ++i) o[6 + i] = (float)log(fmax((double)q(ps[i]), 1e-12 * T) / meanGap);
+        for (int i = 0; i < 5; ++i) o[6 + i] = (float)log(fmax((double)q(i), 1e-12 * T) / meanGap);
         o[11] = (float)(s2 / T);
         o[12] = (float)(s10 / T);
         o[13] = (float)(s100 / T);
@@ -275,8 +347,8 @@ int window_occupancy(int F) {
 
 size_t features_smem_bytes(int64_t max_n) {
     int64_t P2 = 1;
-    while (P2 < max_n - 1) P2 <<= 1;
-    return (size_t)P2 * sizeof(float);
+    while (P2 < max_n - 1 && P2 < kSortMaxGaps) P2 <<= 1;
+    return std::max((size_t)P2 * sizeof(float), (size_t)5 * 256 * sizeof(unsigned));
 }
 
 cudaError_t launch_features(int n_patterns, int64_t max_n, const double* t, const int64_t* off, const double* f0,

@@ -129,8 +129,9 @@ lsp_status lsp_fap_features(lsp_ctx* ctx, int32_t n, const int64_t* t_off, const
     int64_t max_n = 0;
     for (int c = 0; c < n; ++c) {
         const int64_t len = off[c + 1] - off[c];
-        if (len < 2 || len > 32769)
-            return fail(ctx, LSP_ERR_INVALID_ARG, "pattern %d has %lld samples (2..32769 allowed)", c, (long long)len);
+        if (len < 2 || len >= (int64_t(1) << 31))
+            return fail(ctx, LSP_ERR_INVALID_ARG, "pattern %d has %lld samples (2 .. 2^31 - 1 allowed)", c,
+                        (long long)len);
         if (nf[c] < 1 || nf[c] >= (int64_t(1) << 31) || !(dfv[c] > 0.0) || !std::isfinite(f0v[c]) ||
             !std::isfinite(dfv[c]) || f0v[c] < 0.0)
             return fail(ctx, LSP_ERR_INVALID_ARG, "grid of pattern %d must have N_f >= 1, df > 0, f_0 >= 0", c);

@@ -62,6 +62,39 @@ def test_features_match_oracle(ctx):
     assert np.array_equal(gd.cpu().numpy(), got)
 
 
+def _long_patterns():
+    """Patterns on both sides of the shared-memory sort's 32,768 gaps, longer
+    random ones with exponential gaps (neighbouring order statistics well
+    apart, so a rank off by one shows), and the paper-shape cadence."""
+    from paper_1007_1658_gb300 import synth
+    rng = np.random.default_rng(5150)
+    ts = [np.sort(rng.uniform(0.0, 300.0, 32_769)), np.sort(rng.uniform(0.0, 300.0, 32_770)),
+          np.cumsum(rng.exponential(0.01, 60_001)), np.cumsum(rng.exponential(0.02, 120_000))]
+    ts.append(synth.corot_382k().t)
+    return ts
+
+
+def test_features_of_long_patterns_match_oracle(ctx):
+    """Patterns of more than 32,769 samples take the radix select of the five
+    cadence order statistics instead of the shared-memory sort; both paths
+    against the oracle, and the quantile features against the FP32 gaps'
+    exact order statistics (to one float ulp of the log)."""
+    ts = _long_patterns()
+    off = np.concatenate([[0], np.cumsum([t.size for t in ts])]).astype(np.int64)
+    nf = np.array([1500] * len(ts), np.int64)  # a short window grid keeps the oracle quick
+    df = np.array([1.0 / (4.0 * (t[-1] - t[0])) for t in ts])
+    got = ctx.fap_features(off, np.concatenate(ts), df.copy(), df, nf)
+    for c, t in enumerate(ts):
+        ref = S.features(t, df[c], df[c], nf[c])
+        _check_features(got[c].astype(np.float64), ref)
+        g32 = np.sort(np.diff(t).astype(np.float32))
+        M, T = g32.size, t[-1] - t[0]
+        for i, p in enumerate((0.05, 0.25, 0.5, 0.75, 0.95)):
+            q = float(g32[int(np.floor(p * (M - 1)))])
+            want = np.float32(np.log(max(q, 1e-12 * T) / (T / M)))
+            assert abs(got[c, 6 + i] - want) <= 1.2e-7 * max(1.0, abs(want)), (c, p, got[c, 6 + i], want)
+
+
 def test_features_even_grid_and_unsorted(ctx, lsp):
     N, dt = 400, 0.25
     t = np.arange(N) * dt
@@ -75,6 +108,16 @@ def test_features_even_grid_and_unsorted(ctx, lsp):
     bad[[10, 11]] = bad[[11, 10]]
     with pytest.raises(lsp.LspError) as e:
         ctx.fap_features(np.array([0, N], np.int64), bad, np.array([df]), np.array([df]), np.array([2 * N], np.int64))
+        ctx.sync(10.0)
+    assert e.value.status == lsp.ERR_NONFINITE
+    # the same on the radix-select path (more than 32,769 samples)
+    N2 = 40_000
+    bad2 = np.arange(N2) * dt
+    bad2[[30_000, 30_001]] = bad2[[30_001, 30_000]]
+    df2 = 1.0 / (4 * (N2 - 1) * dt)
+    with pytest.raises(lsp.LspError) as e:
+        ctx.fap_features(np.array([0, N2], np.int64), bad2, np.array([df2]), np.array([df2]),
+                         np.array([500], np.int64))
         ctx.sync(10.0)
     assert e.value.status == lsp.ERR_NONFINITE
 
