@@ -84,10 +84,10 @@ __device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, in
             if (live) strip_tile<T, false>(st, a, bb, n, k0);
         });
     } else {
+        // x of this realization from its own staged row
+        constexpr int T = sizeof(sm.A[0]) / sizeof(uint4);
         for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
-            if (!live) return;
-#pragma unroll 2
-            for (int j = 0; j < n; ++j) st.template add<false>(a[j], bb[j], xs[j], k0);
+            if (live) strip_tile<T, false>(st, a, bb, xs, n, k0);
         });
     }
     const float n = (float)(e - b);
