@@ -63,6 +63,42 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
     return a > b ? a : b;
 }
 
+// The double-buffered cp.async tile loop of for_each_tile for a realization
+// whose x is not the one the records carry: each sample's second record is
+// staged as {x[j], cos 2 pi u, sin 2 pi u, 2 cos 2 pi u}, x taken from the
+// realization's row, so the strip reads it exactly as it reads the records'
+// own x.  Reading x with a load of its own instead measured 0.63 against 0.81
+// of the FMA roof (ncu: dispatch stalls 1.33 against 0.19 per issue).
+template <int TILE, class Body>
+__device__ __forceinline__ void for_each_tile_xb(TileSmem<false, TILE>& sm, const uint4* __restrict__ recA,
+                                                 const float4* __restrict__ recB, const float* __restrict__ x,
+                                                 int64_t j0, int64_t j1, Body&& body) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntiles = j1 > j0 ? (int)((j1 - j0 + TILE - 1) / TILE) : 0;
+    auto stage = [&](int buf, int64_t jt) {
+        const int n = (int)min((int64_t)TILE, j1 - jt);
+        for (int q = tid; q < n; q += nt) {
+            cp_async16(&sm.A[buf][q], recA + jt + q);
+            float* dst = reinterpret_cast<float*>(&sm.B[buf][q]);
+            const float* src = reinterpret_cast<const float*>(recB + jt + q);
+            cp_async4(dst, x + jt + q);
+            cp_async4(dst + 1, src + 1);
+            cp_async8(dst + 2, src + 2);
+        }
+    };
+    if (ntiles > 0) stage(0, j0);
+    cp_async_commit();
+    for (int it = 0; it < ntiles; ++it) {
+        const int64_t jt = j0 + (int64_t)it * TILE;
+        if (it + 1 < ntiles) stage((it + 1) & 1, jt + TILE);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        body(sm.A[it & 1], sm.B[it & 1], (int)min((int64_t)TILE, j1 - jt));
+        __syncthreads();
+    }
+}
+
 // One work item with strips of FF frequencies starting at k0: the tile loop
 // over all samples of the curve, Eq. 5-6, P written if asked; returns this
 // thread's largest (P bits << 32 | ~k) key.
@@ -84,10 +120,10 @@ __device__ __forceinline__ unsigned long long batch_item(SM& sm, uint32_t k0, in
             if (live) strip_tile<T, false>(st, a, bb, n, k0);
         });
     } else {
-        // x of this realization from its own staged row
+        // x of this realization staged into the records' x slot
         constexpr int T = sizeof(sm.A[0]) / sizeof(uint4);
-        for_each_tile<true>(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, const float* xs, int n) {
-            if (live) strip_tile<T, false>(st, a, bb, xs, n, k0);
+        for_each_tile_xb(sm, recA, recB, x, b, e, [&](const uint4* a, const float4* bb, int n) {
+            if (live) strip_tile<T, false>(st, a, bb, n, k0);
         });
     }
     const float n = (float)(e - b);
@@ -117,7 +153,7 @@ ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __re
                 const uint4* __restrict__ recA, const float4* __restrict__ recB, const float* __restrict__ xr,
                 float* __restrict__ P_out, const int64_t* __restrict__ P_off, int64_t P_total,
                 unsigned long long* __restrict__ maxkey) {
-    __shared__ __align__(16) TileSmem<!XREC, TILE> sm;
+    __shared__ __align__(16) TileSmem<false, TILE> sm;
     __shared__ int s_item;
     __shared__ unsigned long long s_red[kMainThreads / 32];
     for (;;) {

@@ -491,28 +491,6 @@ __device__ __forceinline__ void strip_tile(S& st, const uint4* a, const float4* 
     }
 }
 
-// The same with x from its own staged row (the batch kernels' realizations
-// other than the one the records carry): the records with two 128-bit loads,
-// x with a scalar load, full tiles with a constant trip count.
-template <int TILE, bool C2_REC = true, class S>
-__device__ __forceinline__ void strip_tile(S& st, const uint4* a, const float4* b, const float* x, int n,
-                                           uint32_t k0) {
-    auto sample = [&](int j) {
-        const uint4 A = lds128(a + j);
-        const uint4 Bu = lds128(b + j);
-        const float4 B = make_float4(__uint_as_float(Bu.x), __uint_as_float(Bu.y), __uint_as_float(Bu.z),
-                                     __uint_as_float(Bu.w));
-        st.template add<C2_REC>(A, B, x[j], k0);
-    };
-    if (n == TILE) {
-#pragma unroll 2
-        for (int j = 0; j < TILE; ++j) sample(j);
-    } else {
-#pragma unroll 2
-        for (int j = 0; j < n; ++j) sample(j);
-    }
-}
-
 // Double-buffered cp.async pipeline over the samples [j0, j1) in tiles of
 // TILE samples (kTile unless a kernel is built for another tile length):
 // stages the two 16-byte phase records of every sample and, when `xr` is
