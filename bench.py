@@ -522,8 +522,8 @@ def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
             lsp.SINCOS_RECUR: ("FMA pipe: 6 accumulate + 4 rotation FP32 ops per term, 128/clk/SM", 128.0 / 10),
             lsp.SINCOS_RECUR3: ("FMA pipe: 6 accumulate + 2 three-term FP32 ops per term, 128/clk/SM",
                                 128.0 / 8),
-            lsp.SINCOS_RECUR3_X2: ("FMA pipe: 6 accumulate + 2 three-term FP32 lane ops per term (FFMA2 pairs "
-                                   "+ 2 FFMA), 128/clk/SM", 128.0 / 8)}[mode]
+            lsp.SINCOS_RECUR3_X2: ("FMA pipe: 6 accumulate + 2 three-term FP32 lane ops per term (4 FFMA2), "
+                                   "128/clk/SM", 128.0 / 8)}[mode]
     peak = roof[1] * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
     kernel = "gls_main_kernel<%d,%d>" % (F, {1: 1, 2: 2, 3: 4, 4: 5}[mode])

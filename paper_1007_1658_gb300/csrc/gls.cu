@@ -97,9 +97,12 @@ struct GStrip {
 
 // Packed form of the three-term strip with the sign-folded y_i of
 // Strip<F, kRecur3x2>, here with the (cos, sin) pair in the two lanes: the
-// pairs (XC, XS) and (C, S) take one FFMA2 each per term with the data
-// factors +-x and +-q, CC' and CS' two scalar FFMA, the recurrence one FFMA2.
-// Bit-identical to GStrip<F, kRecur3>.
+// pairs (XC, XS), (C, S) and (CC', CS') take one FFMA2 each per term, with the
+// data factors +-x, +-q and the pair (c, c), the recurrence one FFMA2: no
+// scalar FFMA between the packed ones.  With CC' and CS' as two scalar FFMA
+// instead, the mix measured 5.40 against 4.85 ms on 100,000 x 200,000 (FMA
+// pipe busy 75 % of cycles, math-pipe throttle the top stall).  Bit-identical
+// to GStrip<F, kRecur3>.
 template <int F>
 struct GStrip<F, kRecur3x2> {
     float xc[F], xs[F], c1[F], s1[F], cc[F], cs[F];
@@ -116,8 +119,9 @@ struct GStrip<F, kRecur3x2> {
         const float2 b = __ffma2_rn(qf, y, make_float2(c1[i], s1[i]));
         c1[i] = b.x;
         s1[i] = b.y;
-        cc[i] = fmaf(y.x, y.x, cc[i]);
-        cs[i] = fmaf(y.x, y.y, cs[i]);
+        const float2 d = __ffma2_rn(make_float2(y.x, y.x), y, make_float2(cc[i], cs[i]));
+        cc[i] = d.x;
+        cs[i] = d.y;
     }
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, float q, uint32_t k0) {
