@@ -245,7 +245,8 @@ def run_gpu(args, rank, world, dist):
         return 0
     peaks, peak_src = _peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mode = args.mode if args.mode else lsp.SINCOS_RECUR3
+    # the library's AUTO choice is the packed three-term strip
+    mode = args.mode if args.mode else lsp.SINCOS_RECUR3_X2
     F = args.F if args.F else {lsp.SINCOS_MUFU: 8, lsp.SINCOS_RECUR: 16, lsp.SINCOS_RECUR3: 24,
                                lsp.SINCOS_RECUR3_X2: 24}[mode]
     # algorithmic work per term on the bounding pipe (roof in terms per clock per SM)
@@ -253,8 +254,8 @@ def run_gpu(args, rank, world, dist):
             lsp.SINCOS_RECUR: (8, "FMA pipe: 4 accumulate + 4 rotation FP32 ops per term, 128/clk/SM", 128.0 / 8),
             lsp.SINCOS_RECUR3: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 ops per term, 128/clk/SM",
                                 128.0 / 6),
-            lsp.SINCOS_RECUR3_X2: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 lane ops per term (as FFMA2 "
-                                      "pairs + 2 FFMA), 128/clk/SM", 128.0 / 6)}[mode]
+            lsp.SINCOS_RECUR3_X2: (6, "FMA pipe: 4 accumulate + 2 three-term FP32 lane ops per term (3 FFMA2), "
+                                      "128/clk/SM", 128.0 / 6)}[mode]
     terms_per_clk = roof[2]
     peak = terms_per_clk * sms * peaks["sm_max_mhz"] * 1e6
     achieved = terms / (float(np.mean(main_ms)) * 1e-3)
@@ -715,7 +716,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--mode", type=int, default=0,
-                    help="sin/cos mode: 0 auto, 1 MUFU, 2 recurrence, 3 three-term recurrence")
+                    help="sin/cos mode: 0 auto (= 4), 1 MUFU, 2 recurrence, 3 three-term recurrence, "
+                         "4 three-term recurrence in packed FP32x2")
     ap.add_argument("--F", type=int, default=0, help="frequencies per thread (0 = auto)")
     ap.add_argument("--ref-bins", type=int, default=2048, help="reference arm: oracle frequencies per step")
     ap.add_argument("--cpu-bins", type=int, default=16384, help="cpu_baseline: oracle frequencies (~10-30 s)")

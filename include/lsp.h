@@ -50,21 +50,20 @@ typedef enum lsp_status {
 
 /* How sin/cos of the phase are produced in the O(N_t N_f) loop. */
 typedef enum lsp_sincos_mode {
-    LSP_SINCOS_AUTO = 0,   /* the library's choice (currently RECUR3)                    */
+    LSP_SINCOS_AUTO = 0,   /* the library's choice (currently RECUR3_X2)                 */
     LSP_SINCOS_MUFU = 1,   /* hardware sin/cos (SFU) of every phase (Sec. 4.3's choice)  */
     LSP_SINCOS_RECUR = 2,  /* SFU seed per strip of adjacent frequencies, then the
                               angle-addition rotation by (cos, sin)(2 pi t_j df) on FMA */
     LSP_SINCOS_RECUR3 = 3, /* SFU seed, one rotation, then the three-term form
                               z_{k+1} = 2 cos(2 pi t_j df) z_k - z_{k-1} (half the FMA work
                               of RECUR; error grows faster with the strip length)      */
-    LSP_SINCOS_RECUR3_X2 = 4 /* RECUR3 in packed FP32x2 FMA, the same roundings with
-                              fewer instructions per term: the classic kernels put
-                              the two halves of each strip in the two lanes (results
-                              bit-identical to RECUR3 with strips of half the length),
-                              the floating-mean kernels and the multi-realization
-                              groups that read the window pass the (cos, sin) pair
-                              (bit-identical to RECUR3 at the same length); other
-                              multi-realization groups use the scalar form         */
+    LSP_SINCOS_RECUR3_X2 = 4 /* RECUR3 in packed FP32x2 FMA: the (cos, sin) pair of a
+                              frequency in the two lanes of every FFMA2, each sum pair
+                              and the three-term step one FFMA2, so the same roundings
+                              (results bit-identical to RECUR3 at the same strip
+                              length) in half the instructions; multi-realization
+                              groups that keep their own CC and CS run the scalar
+                              form                                                   */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */
@@ -218,7 +217,7 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  * R = 2, 4, 8), which halves the arithmetic per periodogram.  With
  * n_real >= 3 R, CC and CS (which depend on the sampling pattern only) come
  * from one extra pass per curve instead of from every group, and under the
- * AUTO sin/cos mode the groups then run the packed strip (RECUR3_X2).  Each
+ * AUTO (= RECUR3_X2) sin/cos mode the groups then run the packed strip.  Each
  * (frequency, realization) is computed exactly as the one-at-a-time kernel
  * with the same strip length would.
  * A work item sums over all samples of its curve in FP32 (the batch does not
@@ -269,11 +268,13 @@ lsp_status lsp_autotune(lsp_ctx *ctx, int64_t N_t, int64_t N_f, lsp_options *cho
  * times launch shapes on the caller's own batch description (curves, grids
  * and n_real noise realizations, drawn from a fixed internal seed) and keeps
  * the fastest whose per-periodogram maxima agree with the first shape's to
- * 2e-5 (relative).  Shapes: for n_real = 1, the three-term recurrence with
- * strips of F = 24 or 16 frequencies, tail strips of 8, 4 or none after a
- * curve's last full block, and shared-memory tiles of 128, 256 or 512
- * samples, and the angle-addition recurrence; for n_real > 1, realization
- * groups R = 4 (F = 12 or 8, the three tiles), 2, 8 and 1.  The choice is
+ * 2e-5 (relative).  Shapes: for n_real = 1, the packed three-term recurrence
+ * with strips of F = 24 or 16 frequencies, tail strips of 8, 4 or none after
+ * a curve's last full block, and shared-memory tiles of 128, 256 or 512
+ * samples, the scalar three-term and the angle-addition recurrences at their
+ * default shapes; for n_real > 1, realization groups R = 4 (F = 12 or 8, the
+ * three tiles), 2, 8 and 1, and the packed strips of the groups that read the
+ * window pass.  The choice is
  * remembered for this batch's size bucket (log2 of its terms per
  * realization, log2 of its mean N_t, its realization count 1 / 2-3 / 4-7 / 8+):
  * later lsp_batch calls in that bucket use it when the options leave the
@@ -504,7 +505,7 @@ void lsp_destroy(lsp_ctx *ctx);
  * while they run -- e.g. an application whose memory pool already owns the
  * whole GPU, or a latency-critical loop that cannot afford cudaMalloc's
  * device-wide synchronization.  It computes the same P_out[k] = P_n(f_0 + k df)
- * (three-term recurrence sin/cos, fixed-point phase) without a context and without any
+ * (packed three-term recurrence sin/cos, fixed-point phase) without a context and without any
  * cudaMalloc/cudaFree or allocating library call.
  *
  * Scratch: one file-scope device array of 64 MiB + 8 KiB that every GPU which

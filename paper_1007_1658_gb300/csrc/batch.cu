@@ -20,8 +20,7 @@ BatchFn batch_fn(int mode, int F, bool xrec, int tailF, int tile) {
         case kModeMufu: return tailF == (F > kBatchTailF ? kBatchTailF : 0) && tile == kTile ? batch_fn_mufu(F, xrec) : nullptr;
         case kModeRecur: return tailF == (F > kBatchTailF ? kBatchTailF : 0) && tile == kTile ? batch_fn_recur(F, xrec) : nullptr;
         case kModeRecur3: return batch_fn_recur3(F, xrec, tailF, tile);
-        case kModeRecur3x2:
-            return tailF == (F > kBatchTailF ? kBatchTailF : 0) && tile == kTile ? batch_fn_recur3x2(F, xrec) : nullptr;
+        case kModeRecur3x2: return batch_fn_recur3x2(F, xrec, tailF, tile);
         default: return nullptr;
     }
 }

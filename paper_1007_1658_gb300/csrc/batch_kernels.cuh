@@ -28,12 +28,13 @@ using BatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const
 
 // Kernel of a single-realization shape (nullptr when it is not built):
 // defaults (tail strips of 8 for F > 8, tiles of kTile) for every mode and
-// strip length, and for the three-term recurrence at F = 16 and 24 with x in
-// the records also tail strips of 0, 4, 8 and tiles of 128, 256, 512.
+// strip length, and for the three-term recurrence (scalar and packed) at
+// F = 16 and 24 with x in the records also tail strips of 0, 4, 8 and tiles
+// of 128, 256, 512.
 BatchFn batch_fn_mufu(int F, bool xrec);
 BatchFn batch_fn_recur(int F, bool xrec);
 BatchFn batch_fn_recur3(int F, bool xrec, int tailF, int tile);
-BatchFn batch_fn_recur3x2(int F, bool xrec);
+BatchFn batch_fn_recur3x2(int F, bool xrec, int tailF, int tile);
 // Multi-realization kernels take two more arguments: the window sums (CC, CS)
 // of every frequency of every curve, curve c's at win[woff[c] + k], which the
 // kernels built with win = true read instead of accumulating (the others
@@ -191,6 +192,30 @@ ls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __re
             if (m) atomicMax(&maxkey[(size_t)w.real * n_curves + w.curve], m);
         }
     }
+}
+
+// The shapes that lsp_autotune_batch may pick for single-realization batches
+// with x in the records besides the default pair (tail 8, tiles of kTile):
+// strips of 16 or 24, tail strips of 0, 4 or 8, tiles of 128, 256 or 512.
+template <int MODE>
+BatchFn batch_fn_tuned(int F, int tailF, int tile) {
+    if (F == 16 && tailF == 0 && tile == 128) return ls_batch_kernel<16, MODE, true, 0, 128>;
+    if (F == 16 && tailF == 0 && tile == 256) return ls_batch_kernel<16, MODE, true, 0, 256>;
+    if (F == 16 && tailF == 0 && tile == 512) return ls_batch_kernel<16, MODE, true, 0, 512>;
+    if (F == 16 && tailF == 4 && tile == 128) return ls_batch_kernel<16, MODE, true, 4, 128>;
+    if (F == 16 && tailF == 4 && tile == 256) return ls_batch_kernel<16, MODE, true, 4, 256>;
+    if (F == 16 && tailF == 4 && tile == 512) return ls_batch_kernel<16, MODE, true, 4, 512>;
+    if (F == 16 && tailF == 8 && tile == 256) return ls_batch_kernel<16, MODE, true, 8, 256>;
+    if (F == 16 && tailF == 8 && tile == 512) return ls_batch_kernel<16, MODE, true, 8, 512>;
+    if (F == 24 && tailF == 0 && tile == 128) return ls_batch_kernel<24, MODE, true, 0, 128>;
+    if (F == 24 && tailF == 0 && tile == 256) return ls_batch_kernel<24, MODE, true, 0, 256>;
+    if (F == 24 && tailF == 0 && tile == 512) return ls_batch_kernel<24, MODE, true, 0, 512>;
+    if (F == 24 && tailF == 4 && tile == 128) return ls_batch_kernel<24, MODE, true, 4, 128>;
+    if (F == 24 && tailF == 4 && tile == 256) return ls_batch_kernel<24, MODE, true, 4, 256>;
+    if (F == 24 && tailF == 4 && tile == 512) return ls_batch_kernel<24, MODE, true, 4, 512>;
+    if (F == 24 && tailF == 8 && tile == 256) return ls_batch_kernel<24, MODE, true, 8, 256>;
+    if (F == 24 && tailF == 8 && tile == 512) return ls_batch_kernel<24, MODE, true, 8, 512>;
+    return nullptr;
 }
 
 // Multi-RHS variant for many realizations of the same patterns: an item is

@@ -103,7 +103,7 @@ ls_window_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         const int64_t b = off[w.curve], e = off[w.curve + 1];
         const int64_t M = nw[w.curve];
         const uint32_t k0 = (uint32_t)w.fblock * (kMainThreads * F) + (uint32_t)threadIdx.x * F;
-        Strip<F, kRecur3> st;
+        Strip<F, kRecur3x2> st;
         st.zero();
         for_each_tile<false>(sm, recA, recB, nullptr, b, e, [&](const uint4* a, const float4* bb, const float*, int n) {
 #pragma unroll 2

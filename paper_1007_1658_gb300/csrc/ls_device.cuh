@@ -203,70 +203,57 @@ struct Strip {
     }
 };
 
-// Packed FP32x2 form of the three-term strip for the four-sum kernels.  The
-// strip's two halves, k0 .. k0+H-1 and k0+H .. k0+F-1 (H = F/2), run side by
-// side in the two lanes of every FFMA2: the recurrence, (XC), (XS), (CC) and
-// (CS) each take one FFMA2 per pair of terms, so a term costs 3 issue slots
-// for the same 6 FMA-pipe lane operations, with no scalar FFMA mixed in.
-// Each half is seeded from its own exact phase.  FFMA2 has no negated addend,
-// so the lanes carry y_i = s_i z_i with signs s = (+, +, -, -, +, +, ...):
-// z_{i+1} = 2C z_i - z_{i-1} becomes y_{i+1} = (i odd ? -2C : 2C) y_i + y_{i-1},
-// and the sign is folded into the data factor (x or -x) of XC and XS; the
-// squares and the product c s do not see it.  Round to nearest is symmetric,
-// so every lane rounds exactly as Strip<F/2, kRecur3> does on that half: the
-// sums are bit-identical to the scalar three-term strip of length F/2.
+// Packed FP32x2 form of the three-term strip for the four-sum kernels: the
+// (cos, sin) pair of a frequency sits in the two lanes of an FFMA2, and every
+// operation of a term is one FFMA2 -- (XC, XS) with the pair (x, x), (CC, CS)
+// with the pair (c, c), and the three-term step -- with no scalar FFMA
+// between them.  FFMA2 has no negated addend, so the lanes carry y_i = g_i z_i
+// with g = (+, +, -, -, +, +, ...): z_{i+1} = 2C z_i - z_{i-1} becomes
+// y_{i+1} = (i odd ? -2C : 2C) y_i + y_{i-1}.  (XC, XS) is kept as g_i times
+// the sums (g_i is the same for every sample) and read back through get();
+// c c and c s do not see the sign.  Round to nearest is symmetric, so every
+// sum is bit for bit Strip<F, kRecur3>'s.
 template <int F>
 struct Strip<F, kRecur3x2> {
-    static_assert(F % 2 == 0, "the packed strip pairs its two halves");
-    static constexpr int H = F / 2;
-    float2 xc2[H], xs2[H], cc2[H], cs2[H];
+    float2 xcs[F], ccs[F];  // g_i (XC, XS) and (CC, CS) of frequency i
 
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int i = 0; i < H; ++i) xc2[i] = xs2[i] = cc2[i] = cs2[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < F; ++i) xcs[i] = ccs[i] = make_float2(0.f, 0.f);
     }
 
     __device__ __forceinline__ void get(int i, float& xc, float& xs, float& cc, float& cs) const {
-        const int h = i < H ? i : i - H;
-        xc = i < H ? xc2[h].x : xc2[h].y;
-        xs = i < H ? xs2[h].x : xs2[h].y;
-        cc = i < H ? cc2[h].x : cc2[h].y;
-        cs = i < H ? cs2[h].x : cs2[h].y;
+        const bool neg = (i >> 1) & 1;
+        xc = neg ? -xcs[i].x : xcs[i].x;
+        xs = neg ? -xcs[i].y : xcs[i].y;
+        cc = ccs[i].x;
+        cs = ccs[i].y;
     }
 
-    __device__ __forceinline__ void acc(int i, float2 xf, float2 yc, float2 ys) {
-        xc2[i] = __ffma2_rn(xf, yc, xc2[i]);
-        xs2[i] = __ffma2_rn(xf, ys, xs2[i]);
-        cc2[i] = __ffma2_rn(yc, yc, cc2[i]);
-        cs2[i] = __ffma2_rn(yc, ys, cs2[i]);
+    __device__ __forceinline__ void acc(int i, float2 xp, float2 y) {
+        xcs[i] = __ffma2_rn(xp, y, xcs[i]);
+        ccs[i] = __ffma2_rn(make_float2(y.x, y.x), y, ccs[i]);
     }
 
     template <bool C2_REC = true>
     __device__ __forceinline__ void add(const uint4& A, const float4& B, float x, uint32_t k0) {
         const float C = B.y, S = B.z, C2 = C2_REC ? B.w : 2.f * B.y;
-        float sa, ca, sb, cb;
-        __sincosf(phase_to_angle(top_phase(A, k0)), &sa, &ca);
-        __sincosf(phase_to_angle(top_phase(A, k0 + H)), &sb, &cb);
-        const float2 xp = make_float2(x, x), xn = make_float2(-x, -x);
-        float2 yc0 = make_float2(ca, cb), ys0 = make_float2(sa, sb);
-        acc(0, xp, yc0, ys0);
-        if (H == 1) return;
+        float s, c;
+        __sincosf(phase_to_angle(top_phase(A, k0)), &s, &c);
+        const float2 xp = make_float2(x, x);
+        float2 y0 = make_float2(c, s);
+        acc(0, xp, y0);
+        if (F == 1) return;
         // first step by angle addition, as the scalar strip takes it
-        const float2 Cp = make_float2(C, C), Sp = make_float2(S, S), Sn = make_float2(-S, -S);
-        float2 yc1 = __ffma2_rn(yc0, Cp, __fmul2_rn(ys0, Sn));
-        float2 ys1 = __ffma2_rn(ys0, Cp, __fmul2_rn(yc0, Sp));
-        acc(1, xp, yc1, ys1);
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, xp, y1);
         const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
 #pragma unroll
-        for (int i = 2; i < H; ++i) {
-            const float2 m = ((i - 1) & 1) ? cn2 : cp2;
-            const float2 yc2 = __ffma2_rn(m, yc1, yc0);
-            const float2 ys2 = __ffma2_rn(m, ys1, ys0);
-            acc(i, ((i >> 1) & 1) ? xn : xp, yc2, ys2);
-            yc0 = yc1;
-            ys0 = ys1;
-            yc1 = yc2;
-            ys1 = ys2;
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            acc(i, xp, y2);
+            y0 = y1;
+            y1 = y2;
         }
     }
 };

@@ -52,11 +52,11 @@ void lsp::host::default_mode_F(const lsp_options& o, int* mode, int* F) {
     } else if (o.sincos_mode == LSP_SINCOS_RECUR) {
         *mode = lsp::kModeRecur;
         *F = 16;
-    } else if (o.sincos_mode == LSP_SINCOS_RECUR3_X2) {
-        *mode = lsp::kModeRecur3x2;
-        *F = 24;
-    } else {
+    } else if (o.sincos_mode == LSP_SINCOS_RECUR3) {
         *mode = lsp::kModeRecur3;
+        *F = 24;
+    } else {  // AUTO and RECUR3_X2: the packed three-term strip, bit-identical to RECUR3 and faster
+        *mode = lsp::kModeRecur3x2;
         *F = 24;
     }
     if (o.freqs_per_thread) *F = o.freqs_per_thread;

@@ -110,12 +110,11 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     // with three groups of realizations or more per pattern, CC and CS come from
     // one window pass per pattern (4 FMA-pipe ops per term) instead of from every
     // group (2 per term and group), which also frees 2F registers per thread
+    // (in the packed mode, the AUTO default, groups that take CC and CS from the
+    // window pass run the packed multi-realization strip, bit-identical to the
+    // scalar one: 256 patterns x 64 realizations at R = 8 131.4 -> 104.2 ms;
+    // groups with their own CC and CS run the scalar strip)
     const bool use_win = R > 1 && n_real >= 3 * R;
-    // groups that take CC and CS from the window pass run the packed strip
-    // (bit-identical to the scalar one; 256 patterns x 64 realizations at R = 8:
-    // 131.4 -> 104.2 ms), unless the options or a tuned shape chose the form
-    if (use_win && !shape && ctx->opt.sincos_mode == LSP_SINCOS_AUTO && mode == lsp::kModeRecur3)
-        mode = lsp::kModeRecur3x2;
     if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile, use_win) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0 ||
         (use_win && lsp::window_occupancy(mode, F) <= 0))
         return fail(ctx, LSP_ERR_UNSUPPORTED, "batch shape (mode %d, F %d, R %d, tail %d, tile %d) is not built", mode,

@@ -100,7 +100,7 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
     float4* recB = (float4*)(base + kHeaderBytes + size_t(kMaxSamples) * 16);
     float* part = (float*)(base + kHeaderBytes + kRecordBytes);
 
-    // Launch shape of the default (three-term recurrence) path: strips of 24
+    // Launch shape of the default (packed three-term recurrence) path: strips of 24
     // frequencies, and an N_t split with chunks of at most kMaxChunk samples
     // (the bound on the FP32 running sums that lsp_periodogram keeps), more
     // where that fills the SMs.  The partial sums of `need` chunks fit the
@@ -116,7 +116,7 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
         const int64_t blocks = (int64_t)(kPartialBytes / (row_bytes * (size_t)need * (size_t)per_block));
         tile = std::min<int64_t>(N_f, blocks * per_block);
     }
-    const int occ = lsp::main_occupancy(lsp::kModeRecur3, F);
+    const int occ = lsp::main_occupancy(lsp::kModeRecur3x2, F);
     const int64_t slots = (int64_t)occ * (sms > 0 ? sms : 1);
 
     // the shared array keeps the last call's contents: clear the status word
@@ -135,7 +135,7 @@ extern "C" lsp_status lsp_periodogram_noalloc(const double* t, const double* X, 
             if (e != cudaSuccess) break;
         }
         lsp::MainShape s{};
-        s.mode = lsp::kModeRecur3;
+        s.mode = lsp::kModeRecur3x2;
         s.F = F;
         s.nfb = (int)((nf + per_block - 1) / per_block);
         s.nf_pad = (int64_t)s.nfb * per_block;

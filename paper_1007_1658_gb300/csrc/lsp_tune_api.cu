@@ -124,9 +124,9 @@ extern "C" lsp_status lsp_autotune(lsp_ctx* ctx, int64_t N_t, int64_t N_f, lsp_o
     float pmax = 0.f;
     for (float v : ref) pmax = std::max(pmax, v);
     struct Cand { int sincos, F; };
-    const Cand cands[] = {{LSP_SINCOS_RECUR3, 24}, {LSP_SINCOS_RECUR3, 16}, {LSP_SINCOS_RECUR3, 8},
-                          {LSP_SINCOS_RECUR3, 4},  {LSP_SINCOS_RECUR, 16},  {LSP_SINCOS_RECUR, 8},
-                          {LSP_SINCOS_MUFU, 8}};
+    const Cand cands[] = {{LSP_SINCOS_RECUR3_X2, 24}, {LSP_SINCOS_RECUR3_X2, 16}, {LSP_SINCOS_RECUR3_X2, 8},
+                          {LSP_SINCOS_RECUR3_X2, 4},  {LSP_SINCOS_RECUR3, 24},    {LSP_SINCOS_RECUR, 16},
+                          {LSP_SINCOS_RECUR, 8},      {LSP_SINCOS_MUFU, 8}};
     TuneEntry best{bucket(N_t), bucket(N_f), 0, 0, 0, 1e30f};
     for (const Cand& c : cands) {
         // the heuristic split of this candidate, then half and double of it
@@ -228,9 +228,12 @@ extern "C" lsp_status lsp_autotune_batch(lsp_ctx* ctx, int32_t n_curves, const i
     std::vector<BatchShape> cands;
     using lsp::kModeRecur3;
     if (n_real == 1) {
+        // the packed strip in every tuned shape; the scalar one, bit-identical
+        // and slower, at the default shape only
         for (int F : {24, 16})
             for (int tail : {8, 4, 0})
-                for (int tile : {128, 256, 512}) cands.push_back({kModeRecur3, F, 1, tail, tile});
+                for (int tile : {128, 256, 512}) cands.push_back({lsp::kModeRecur3x2, F, 1, tail, tile});
+        cands.push_back({kModeRecur3, 24, 1, 8, lsp::kTile});
         cands.push_back({lsp::kModeRecur, 16, 1, 8, lsp::kTile});
     } else {
         for (int tile : {128, 256, 512}) {

@@ -252,7 +252,8 @@ def test_autotune_choice_is_used_and_accurate(lsp):
     ctx = lsp.Context(0)
     c = synth.plain_1k()
     chosen = ctx.autotune(c.t.size, c.nf)
-    assert chosen["sincos_mode"] in (1, 2, 3) and chosen["freqs_per_thread"] in (4, 8, 16, 24) and chosen["split"] >= 1
+    assert chosen["sincos_mode"] in (1, 2, 3, 4) and chosen["freqs_per_thread"] in (4, 8, 16, 24)
+    assert chosen["split"] >= 1
     ref = oracle.periodogram(c.t, c.X, c.f0, c.df, c.nf)
     got = _run(ctx, c.t, c.X, c.f0, c.df, c.nf)  # AUTO: takes the tuned entry
     assert_parity(got, ref, what="autotuned plain_1k %s" % chosen)
@@ -321,19 +322,22 @@ def test_even_grid_noise_maxima_follow_the_exact_dirichlet_law(ctx):
         assert abs((1 - Q) - p) < 0.08, (p, Q)
 
 
-@pytest.mark.parametrize("F", [8, 16, 24])
+@pytest.mark.parametrize("F", [4, 8, 16, 20, 24, 28])
 def test_packed_recurrence_is_bit_identical_to_scalar(ctx, F):
-    """RECUR3_X2 runs the two halves of a strip of F frequencies in the two
-    lanes of packed FP32x2 FMA with sign-folded steps; every lane must round
-    exactly as the scalar three-term form does on a strip of F/2."""
+    """RECUR3_X2 (the AUTO default) carries the (cos, sin) pair of a frequency
+    in the two lanes of packed FP32x2 FMA, with sign-folded steps and sums;
+    every lane must round exactly as the scalar three-term form does on the
+    same strip, with and without an N_t split."""
     from paper_1007_1658_gb300 import synth
     c = synth.gapped_100k()
     nf = 40_000
     outs = []
-    for mode, f in ((3, F // 2), (4, F)):
+    for mode in (3, 4):
         for split in (1, 6):
-            outs.append(_run(ctx, c.t, c.X, c.f0, c.df, nf, sincos_mode=mode, freqs_per_thread=f, split=split))
+            outs.append(_run(ctx, c.t, c.X, c.f0, c.df, nf, sincos_mode=mode, freqs_per_thread=F, split=split))
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
+    # AUTO picks the packed strip
+    assert np.array_equal(_run(ctx, c.t, c.X, c.f0, c.df, nf, sincos_mode=0, freqs_per_thread=F, split=6), outs[3])
 
 
 @pytest.mark.parametrize("kind", ["classic", "floating_mean"])

@@ -75,8 +75,9 @@ def test_tuned_batch_uses_its_shape_and_matches_the_oracle(lsp, tmp_path, n_real
 
 
 def test_tuned_shapes_agree_with_the_default_and_the_oracle(lsp):
-    """Every single-realization shape the tuner may pick gives the oracle's
-    periodogram (full P of a few curves) and the same maxima as the default."""
+    """Every single-realization shape the tuner may pick, in the packed
+    (internal mode 5) and scalar (4) three-term forms, gives the oracle's
+    periodogram (full P of a few curves) and the same maxima as the first."""
     b, args = _batch(n=24, seed=616)
     P_off = np.zeros(b.n + 1, np.int64)
     P_off[1:] = np.cumsum(b.nf)
@@ -87,38 +88,37 @@ def test_tuned_shapes_agree_with_the_default_and_the_oracle(lsp):
             for c in (0, 11, b.n - 1)}
     base = None
     path_dir = os.environ.get("TMPDIR", "/tmp")
-    for F in (24, 16):
-        for tail in (8, 4, 0):
-            for tile in (256, 128, 512):
-                ctx = lsp.Context(0)
-                # write a one-entry tuning file for this bucket, then load it
-                ctx.autotune_batch(*args, n_real=1)
-                path = os.path.join(path_dir, "lsp_tune_%d_%d_%d_%d.json" % (os.getpid(), F, tail, tile))
-                ctx.tune_save(path)
-                doc, entries = _batch_entries(path)
-                entries[0].update(mode=4, F=F, R=1, tailF=tail, tile=tile)
-                with open(path, "w") as fh:
-                    fh.write('{"lsp_tune": 1, "device": "%s", "entries": [\n' % doc["device"])
-                    fh.write(json.dumps(entries[0]) + "\n]}\n")
-                ctx2 = lsp.Context(0)
-                assert ctx2.tune_load(path) == 1
-                os.remove(path)
-                P = torch.empty(int(P_off[-1]), dtype=torch.float32, device="cuda")
-                maxP, _ = ctx2.batch(args[0], args[1], args[2], args[3], args[4], X=X_d, P_out=P, P_off=P_off_d,
-                                     maxP=torch.empty(b.n, dtype=torch.float32, device="cuda"),
-                                     argmax=torch.empty(b.n, dtype=torch.int32, device="cuda"))
-                ctx2.sync(120.0)
-                assert ctx2.test_last_batch_shape() == (4, F, 1, tail, tile)
-                Pn = P.cpu().numpy()
-                for c, ref in refs.items():
-                    assert_parity(Pn[P_off[c]:P_off[c] + b.nf[c]], ref, what="F %d tail %d tile %d curve %d"
-                                  % (F, tail, tile, c))
-                m = maxP.cpu().numpy().astype(np.float64)
-                if base is None:
-                    base = m
-                assert np.max(np.abs(m - base) / base) <= 2e-5
-                ctx.close()
-                ctx2.close()
+    for mode, F, tail, tile in [(m, F, tail, tile) for m in (5, 4) for F in (24, 16) for tail in (8, 4, 0)
+                                for tile in (256, 128, 512)]:
+        ctx = lsp.Context(0)
+        # write a one-entry tuning file for this bucket, then load it
+        ctx.autotune_batch(*args, n_real=1)
+        path = os.path.join(path_dir, "lsp_tune_%d_%d_%d_%d_%d.json" % (os.getpid(), mode, F, tail, tile))
+        ctx.tune_save(path)
+        doc, entries = _batch_entries(path)
+        entries[0].update(mode=mode, F=F, R=1, tailF=tail, tile=tile)
+        with open(path, "w") as fh:
+            fh.write('{"lsp_tune": 1, "device": "%s", "entries": [\n' % doc["device"])
+            fh.write(json.dumps(entries[0]) + "\n]}\n")
+        ctx2 = lsp.Context(0)
+        assert ctx2.tune_load(path) == 1
+        os.remove(path)
+        P = torch.empty(int(P_off[-1]), dtype=torch.float32, device="cuda")
+        maxP, _ = ctx2.batch(args[0], args[1], args[2], args[3], args[4], X=X_d, P_out=P, P_off=P_off_d,
+                             maxP=torch.empty(b.n, dtype=torch.float32, device="cuda"),
+                             argmax=torch.empty(b.n, dtype=torch.int32, device="cuda"))
+        ctx2.sync(120.0)
+        assert ctx2.test_last_batch_shape() == (mode, F, 1, tail, tile)
+        Pn = P.cpu().numpy()
+        for c, ref in refs.items():
+            assert_parity(Pn[P_off[c]:P_off[c] + b.nf[c]], ref, what="mode %d F %d tail %d tile %d curve %d"
+                          % (mode, F, tail, tile, c))
+        m = maxP.cpu().numpy().astype(np.float64)
+        if base is None:
+            base = m
+        assert np.max(np.abs(m - base) / base) <= 2e-5
+        ctx.close()
+        ctx2.close()
 
 
 def test_tuning_file_of_another_gpu_is_not_applied(lsp, tmp_path):
