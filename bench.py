@@ -579,11 +579,11 @@ def mrhs_ops_per_term(R, n_real):
     """FMA-pipe operations per term and realization of an lsp_batch call with
     groups of R realizations: 6 one at a time; else 2 (XC, XS) + 2 recurrence
     shared by the group, plus CC and CS either in every group (2 / R) or, with
-    three groups or more per pattern, once per pattern in the window pass
+    four groups or more per pattern, once per pattern in the window pass
     (4 / n_real)."""
     if R == 1:
         return 6.0
-    if n_real >= 3 * R:
+    if n_real >= 4 * R:
         return 2.0 + 2.0 / R + 4.0 / n_real
     return 2.0 + 4.0 / R
 

@@ -61,9 +61,7 @@ typedef enum lsp_sincos_mode {
                               frequency in the two lanes of every FFMA2, each sum pair
                               and the three-term step one FFMA2, so the same roundings
                               (results bit-identical to RECUR3 at the same strip
-                              length) in half the instructions; multi-realization
-                              groups that keep their own CC and CS run the scalar
-                              form                                                   */
+                              length) in half the instructions                       */
 } lsp_sincos_mode;
 
 /* How the phase f_k t_j is formed. */
@@ -211,13 +209,13 @@ lsp_status lsp_press_rybicki(lsp_ctx *ctx, const double *t, const double *X, int
  *   the largest P of each periodogram and its bin k (lowest k on ties; -1 and
  *   0 for a curve with N_f = 0).
  * With n_real > 1, groups of R realizations (the batch_rhs option; auto: 8
- * when n_real >= 24, else 4) share each pass over a curve's samples: the
+ * when n_real >= 8, else 4) share each pass over a curve's samples: the
  * phase, the sin/cos recurrence and CC, CS are computed once for the group
  * and only XC, XS per realization (strips of 16, 12, 8 frequencies for
  * R = 2, 4, 8), which halves the arithmetic per periodogram.  With
- * n_real >= 3 R, CC and CS (which depend on the sampling pattern only) come
- * from one extra pass per curve instead of from every group, and under the
- * AUTO (= RECUR3_X2) sin/cos mode the groups then run the packed strip.  Each
+ * n_real >= 4 R, CC and CS (which depend on the sampling pattern only) come
+ * from one extra pass per curve instead of from every group.  Under the AUTO
+ * (= RECUR3_X2) sin/cos mode the groups run the packed strip.  Each
  * (frequency, realization) is computed exactly as the one-at-a-time kernel
  * with the same strip length would.
  * A work item sums over all samples of its curve in FP32 (the batch does not

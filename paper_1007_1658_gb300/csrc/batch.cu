@@ -28,9 +28,7 @@ BatchFn batch_fn(int mode, int F, bool xrec, int tailF, int tile) {
 MrhsFn mrhs_fn(int mode, int F, int R, int tile, bool win) {
     switch (mode) {
         case kModeRecur3: return mrhs_fn_recur3(F, R, tile, win);
-        // the packed strip leaves CC and CS to the window pass; with its own CC/CS
-        // a group runs the scalar strip
-        case kModeRecur3x2: return win ? mrhs_fn_recur3x2(F, R, tile) : mrhs_fn_recur3(F, R, tile, false);
+        case kModeRecur3x2: return mrhs_fn_recur3x2(F, R, tile, win);
         case kModeMufu:
         case kModeRecur: return tile == kTile ? mrhs_fn_other(mode, F, R, win) : nullptr;
         default: return nullptr;

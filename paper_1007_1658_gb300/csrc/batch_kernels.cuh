@@ -47,10 +47,10 @@ using MrhsFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const 
 // tiles of 256 and 512; each with and without the window sums from WStrip.
 MrhsFn mrhs_fn_recur3(int F, int R, int tile, bool win);
 MrhsFn mrhs_fn_other(int mode, int F, int R, bool win);
-// The same with the three-term recurrence in packed FP32x2 (MStrip<F, R, kRecur3x2,
-// false>); only with the window sums, for the (F, R) shapes of the scalar
-// kernels and tiles of kTile.
-MrhsFn mrhs_fn_recur3x2(int F, int R, int tile);
+// The same with the three-term recurrence in packed FP32x2 (MStrip<F, R,
+// kRecur3x2, !win>), for the (F, R) shapes of the scalar kernels and tiles of
+// kTile.
+MrhsFn mrhs_fn_recur3x2(int F, int R, int tile, bool win);
 // The window pass (ls_window_kernel) for the strip lengths above.
 using WindowFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const int64_t*,
                           const uint4*, const float4*, float2*);
@@ -343,8 +343,8 @@ ls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __res
                         cc_k = w2.x;
                         cs_k = w2.y;
                     } else {
-                        cc_k = st.cc[i];
-                        cs_k = st.cs[i];
+                        cc_k = st.get_cc(i);
+                        cs_k = st.get_cs(i);
                     }
                     const float p = periodogram_value(st.get_xc(i, r), st.get_xs(i, r), cc_k, cs_k, n);
                     if (P) P[k] = p;

@@ -281,6 +281,8 @@ struct MStrip {
 
     __device__ __forceinline__ float get_xc(int i, int r) const { return xc[i][r]; }
     __device__ __forceinline__ float get_xs(int i, int r) const { return xs[i][r]; }
+    __device__ __forceinline__ float get_cc(int i) const { return cc[i]; }
+    __device__ __forceinline__ float get_cs(int i) const { return cs[i]; }
 
     __device__ __forceinline__ void acc(int i, const float (&x)[R], float c, float s) {
 #pragma unroll
@@ -332,33 +334,40 @@ struct MStrip {
     }
 };
 
-// Packed form of the multi-realization strip without CC and CS (the window
-// sums come from WStrip): the (cos, sin) pair of a frequency sits in the two
-// lanes of an FFMA2, so (XC, XS) of one realization take one FFMA2 per term
-// and the three-term step one FFMA2 for both lanes; per term and realization
-// the FMA pipe does the same 2 + 2/R lane operations in half the issue slots.
-// FFMA2 has no negated addend, so the lanes carry y_i = g_i z_i with the signs
+// Packed form of the multi-realization strip: the (cos, sin) pair of a
+// frequency sits in the two lanes of an FFMA2, so (XC, XS) of one realization
+// take one FFMA2 per term, (CC, CS) -- when the strip keeps them (CCS) -- one
+// FFMA2 with the pair (c, c), and the three-term step one FFMA2 for both
+// lanes: the FMA pipe does the same lane operations as the scalar strip in
+// half the issue slots, with no scalar FFMA between the packed ones.  FFMA2
+// has no negated addend, so the lanes carry y_i = g_i z_i with the signs
 // g = (+, +, -, -, +, +, ...) of the other packed strips, and the running sums
 // are kept as g_i (XC, XS): g_i is the same for every sample, and round to
 // nearest is symmetric, so g_i times the sums is bit for bit
-// MStrip<F, R, kRecur3, false>'s XC and XS.
-template <int F, int R>
-struct MStrip<F, R, kRecur3x2, false> {
-    float2 a[F][R];  // g_i (XC, XS) of frequency i, realization r
+// MStrip<F, R, kRecur3, CCS>'s XC and XS (c c and c s do not see the sign).
+template <int F, int R, bool CCS>
+struct MStrip<F, R, kRecur3x2, CCS> {
+    float2 a[F][R];                // g_i (XC, XS) of frequency i, realization r
+    float2 w[CCS ? F : 1];         // (CC, CS) of frequency i
 
     __device__ __forceinline__ void zero() {
 #pragma unroll
-        for (int i = 0; i < F; ++i)
+        for (int i = 0; i < F; ++i) {
+            if (CCS) w[i] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int r = 0; r < R; ++r) a[i][r] = make_float2(0.f, 0.f);
+        }
     }
 
     __device__ __forceinline__ float get_xc(int i, int r) const { return ((i >> 1) & 1) ? -a[i][r].x : a[i][r].x; }
     __device__ __forceinline__ float get_xs(int i, int r) const { return ((i >> 1) & 1) ? -a[i][r].y : a[i][r].y; }
+    __device__ __forceinline__ float get_cc(int i) const { return CCS ? w[i].x : 0.f; }
+    __device__ __forceinline__ float get_cs(int i) const { return CCS ? w[i].y : 0.f; }
 
     __device__ __forceinline__ void acc(int i, const float2 (&xp)[R], float2 y) {
 #pragma unroll
         for (int r = 0; r < R; ++r) a[i][r] = __ffma2_rn(xp[r], y, a[i][r]);
+        if (CCS) w[i] = __ffma2_rn(make_float2(y.x, y.x), y, w[i]);
     }
 
     __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], uint32_t k0) {

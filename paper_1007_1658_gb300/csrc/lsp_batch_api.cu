@@ -71,11 +71,11 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     if (mode == lsp::kModeNaive)
         return fail(ctx, LSP_ERR_UNSUPPORTED, "lsp_batch does not offer the naive FP32 phase");
     // realizations per pass over the samples (multi-RHS) and the strip length that goes with it
-    // (auto: 8 when that makes three groups or more, so that the window pass
-    // and the packed strips serve them; else 4)
+    // (auto: 8 from 8 realizations on -- 4096 patterns x 8 realizations in one
+    // packed group of 8 took 224 ms against 2 x 138 for groups of 4 -- else 4)
     int R = 1;
     if (n_real > 1) {
-        R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : (n_real >= 24 ? 8 : 4);
+        R = ctx->opt.batch_rhs ? ctx->opt.batch_rhs : (n_real >= 8 ? 8 : 4);
         if (R > n_real) R = n_real >= 8 ? 8 : (n_real >= 4 ? 4 : 2);
     }
     // strip lengths measured best on GB300 for each group size (256 patterns x 64 realizations)
@@ -107,14 +107,18 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
         }
     }
     const bool xrec = n_real == 1;  // x travels inside the sample records
-    // with three groups of realizations or more per pattern, CC and CS come from
+    // with four groups of realizations or more per pattern, CC and CS come from
     // one window pass per pattern (4 FMA-pipe ops per term) instead of from every
     // group (2 per term and group), which also frees 2F registers per thread
-    // (in the packed mode, the AUTO default, groups that take CC and CS from the
-    // window pass run the packed multi-realization strip, bit-identical to the
-    // scalar one: 256 patterns x 64 realizations at R = 8 131.4 -> 104.2 ms;
-    // groups with their own CC and CS run the scalar strip)
-    const bool use_win = R > 1 && n_real >= 3 * R;
+    // (in the packed mode, the AUTO default, the groups run the packed
+    // multi-realization strip, bit-identical to the scalar one: 256 patterns x
+    // 64 realizations at R = 8 131.4 -> 104.2 ms with the window sums, 4096
+    // patterns x 8 realizations 285.1 -> 224.1 ms with their own).  The window
+    // pass pays from four groups per pattern on: 256 patterns at R = 8, with
+    // and without it, 3 groups 42.4 / 41.0 ms, 4 groups 54.7 / 54.6, 5 groups
+    // 67.1 / 68.0, 8 groups 104.2 / 108.6; at R = 4, 3 groups 26.3 / 25.4,
+    // 4 groups 33.2 / 33.6.
+    const bool use_win = R > 1 && n_real >= 4 * R;
     if ((R > 1 ? lsp::mrhs_occupancy(mode, F, R, tile, use_win) : lsp::batch_occupancy(mode, F, xrec, tailF, tile)) <= 0 ||
         (use_win && lsp::window_occupancy(mode, F) <= 0))
         return fail(ctx, LSP_ERR_UNSUPPORTED, "batch shape (mode %d, F %d, R %d, tail %d, tile %d) is not built", mode,

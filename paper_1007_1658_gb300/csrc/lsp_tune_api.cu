@@ -244,11 +244,9 @@ extern "C" lsp_status lsp_autotune_batch(lsp_ctx* ctx, int32_t n_curves, const i
         cands.push_back({kModeRecur3, 4, 8, 0, lsp::kTile});
         cands.push_back({kModeRecur3, 8, 8, 0, lsp::kTile});
         cands.push_back({kModeRecur3, 24, 1, 8, lsp::kTile});
-        // the packed strips of groups that take CC and CS from the window pass
-        // (with fewer than three groups a packed shape runs the scalar strip)
+        // the packed strips of the same groups
         const int packed[][2] = {{12, 4}, {8, 4}, {16, 2}, {4, 8}, {8, 8}};
-        for (const auto& fr : packed)
-            if (n_real >= 3 * fr[1]) cands.push_back({lsp::kModeRecur3x2, fr[0], fr[1], 0, lsp::kTile});
+        for (const auto& fr : packed) cands.push_back({lsp::kModeRecur3x2, fr[0], fr[1], 0, lsp::kTile});
     }
     const lsp_options saved = ctx->opt;
     lsp_options o = saved;

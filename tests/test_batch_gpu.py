@@ -63,18 +63,19 @@ def _oracle_noise_curve(b, seed, c, r):
     return t, X
 
 
-@pytest.mark.parametrize("mode,n_real", [(4, 3), (3, 3), (2, 3), (1, 3), (4, 13), (3, 13), (2, 13), (1, 13),
-                                         (0, 13), (0, 27)])
-def test_noise_batch_matches_oracle(ctx, lsp, mode, n_real):
+@pytest.mark.parametrize("mode,n_real,rhs", [(4, 3, 0), (3, 3, 0), (2, 3, 0), (1, 3, 0), (4, 19, 4), (3, 19, 4),
+                                             (2, 19, 4), (1, 19, 4), (0, 13, 0), (0, 35, 0)])
+def test_noise_batch_matches_oracle(ctx, lsp, mode, n_real, rhs):
     """Every (curve, realization) periodogram of a noise batch against the
     oracle on the same Philox noise.  n_real = 3 runs groups of 2 realizations
-    that accumulate their own CC and CS; n_real = 13 runs groups of 4 (the last
-    one partial) that take CC and CS from the window pass, in the packed strip
-    under the automatic and packed modes; n_real = 27 runs the automatic
-    groups of 8 (packed, the last group partial)."""
+    that accumulate their own CC and CS; n_real = 19 at batch_rhs 4 runs five
+    groups of 4 (the last one partial) that take CC and CS from the window
+    pass; under the automatic mode (packed strips) n_real = 13 runs groups of
+    8 with their own CC and CS and n_real = 35 groups of 8 that read the
+    window pass, the last group partial in both."""
     b = _small_batch()
     seed = 99
-    ctx.set_options(sincos_mode=mode)
+    ctx.set_options(sincos_mode=mode, batch_rhs=rhs)
     P_off = np.zeros(b.n + 1, np.int64)
     P_off[1:] = np.cumsum(b.nf)
     P = torch.empty(n_real * int(P_off[-1]), dtype=torch.float32, device="cuda")
@@ -181,14 +182,14 @@ def test_noise_periodograms_follow_the_beta_law(ctx):
 
 
 @pytest.mark.parametrize("packed", [False, True])
-@pytest.mark.parametrize("groups", [1, 3])
+@pytest.mark.parametrize("groups", [1, 4])
 @pytest.mark.parametrize("R,F", [(2, 8), (2, 16), (4, 8), (4, 12), (8, 4), (8, 8)])
 def test_multi_rhs_equals_one_realization_at_a_time(lsp, R, F, groups, packed):
     """Groups of R realizations share the phase, the recurrence and CC/CS; each
     (frequency, realization) must come out bit for bit as the one-at-a-time
     kernel with the same strip length computes it (here with a partial last
     group).  With one full group per pattern the groups accumulate CC and CS
-    themselves; with three or more they read them from the window pass, which
+    themselves; with four or more they read them from the window pass, which
     runs strips of the same length, and in the packed mode run the packed
     strip (the (cos, sin) pair in the two FFMA2 lanes, signs folded into the
     sums).  With strips longer than 8 the one-at-a-time kernel runs the

@@ -15,11 +15,12 @@ import bench  # noqa: E402
 def test_mrhs_ops_per_term_counts_each_sum_once():
     # one at a time: 4 accumulate + 2 three-term FMA per term
     assert bench.mrhs_ops_per_term(1, 64) == 6.0
-    # fewer than three groups: every group keeps CC and CS (2 + (2 + 2) / R)
+    # fewer than four groups: every group keeps CC and CS (2 + (2 + 2) / R)
     assert bench.mrhs_ops_per_term(4, 8) == 3.0
+    assert bench.mrhs_ops_per_term(4, 12) == 3.0
     assert bench.mrhs_ops_per_term(2, 4) == 4.0
-    # three groups or more: CC and CS once per pattern (4 / n_real)
-    assert bench.mrhs_ops_per_term(4, 12) == pytest.approx(2.0 + 0.5 + 4.0 / 12)
+    # four groups or more: CC and CS once per pattern (4 / n_real)
+    assert bench.mrhs_ops_per_term(4, 16) == pytest.approx(2.0 + 0.5 + 4.0 / 16)
     assert bench.mrhs_ops_per_term(4, 64) == pytest.approx(2.5625)
     assert bench.mrhs_ops_per_term(8, 64) == pytest.approx(2.3125)
     # sharing never costs more than one at a time

@@ -117,12 +117,12 @@ def _slack_intact(P_int, b, P_off, n_real):
     return True
 
 
-@pytest.mark.parametrize("n_real,rhs", [(1, 0), (3, 0), (13, 0), (13, 8), (27, 0)])
+@pytest.mark.parametrize("n_real,rhs", [(1, 0), (3, 0), (13, 0), (19, 4), (35, 0)])
 def test_batch_writes_only_its_bins(lsp, n_real, rhs):
-    """Noise batch: single realization, groups with their own CC/CS (3), and
-    groups reading the window pass (13 at R = 4, with a partial last group;
-    13 at R = 8 keeps their own sums; 27 runs the automatic packed groups of
-    8, the last one partial)."""
+    """Noise batch: single realization, groups with their own CC/CS (3 in
+    groups of 2; 13 in the automatic groups of 8, the last partial), and
+    groups reading the window pass (19 at R = 4 and 35 in the automatic
+    groups of 8, each with a partial last group)."""
     b, P_off = _batch_with_slack()
     n = n_real * int(P_off[-1])
     buf, P = _padded(n)

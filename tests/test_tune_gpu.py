@@ -169,9 +169,10 @@ def test_single_curve_tuning_round_trip(lsp, tmp_path):
 def test_tuned_multi_realization_shapes_match_the_oracle(lsp):
     """Multi-realization shapes the tuner may pick, including the tiles of 256
     and 512, every group size and the packed strips (internal mode 5), with 24
-    realizations (three groups or more, so CC and CS come from the window
-    pass): each agrees with the oracle on the maxima of a few (curve,
-    realization) pairs, and with the others."""
+    realizations (four groups or more at R = 2 and 4, so CC and CS come from
+    the window pass; at R = 8 the three groups keep their own): each agrees
+    with the oracle on the maxima of a few (curve, realization) pairs, and
+    with the others."""
     b, args = _batch(n=24, seed=717)
     n_real, seed = 24, 2718
     refs = {}
