@@ -24,8 +24,8 @@ WindowFn window_fn(int mode, int F) {
     switch (mode) {
         case kMufu: return pick_window<kMufu>(F);
         case kRecur: return pick_window<kRecur>(F);
-        case kRecur3:
-        case kRecur3x2: return pick_window<kRecur3>(F);  // as the multi-realization strips: the scalar form
+        case kRecur3: return pick_window<kRecur3>(F);
+        case kRecur3x2: return pick_window<kRecur3x2>(F);  // the same sums, bit for bit
         default: return nullptr;
     }
 }

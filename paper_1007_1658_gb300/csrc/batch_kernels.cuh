@@ -398,7 +398,7 @@ ls_window_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         float2* out = win + woff[w.curve];
 #pragma unroll
         for (int i = 0; i < F; ++i)
-            if (k0 + i < (uint32_t)N_f) out[k0 + i] = make_float2(st.cc[i], st.cs[i]);
+            if (k0 + i < (uint32_t)N_f) out[k0 + i] = make_float2(st.get_cc(i), st.get_cs(i));
     }
 }
 

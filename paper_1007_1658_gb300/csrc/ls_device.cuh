@@ -408,6 +408,9 @@ struct WStrip {
         for (int i = 0; i < F; ++i) cc[i] = cs[i] = 0.f;
     }
 
+    __device__ __forceinline__ float get_cc(int i) const { return cc[i]; }
+    __device__ __forceinline__ float get_cs(int i) const { return cs[i]; }
+
     __device__ __forceinline__ void acc(int i, float c, float s) {
         cc[i] = fmaf(c, c, cc[i]);
         cs[i] = fmaf(c, s, cs[i]);
@@ -449,6 +452,44 @@ struct WStrip {
             }
         }
     }
+};
+
+// Packed form of the window strip: the (cos, sin) pair in the two lanes,
+// (CC, CS) one FFMA2 with the pair (c, c) and the three-term step one FFMA2
+// per term (signs folded into y as in the other packed strips; c c and c s do
+// not see them), bit for bit WStrip<F, kRecur3>'s sums.
+template <int F>
+struct WStrip<F, kRecur3x2> {
+    float2 w[F];  // (CC, CS) of frequency i
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) w[i] = make_float2(0.f, 0.f);
+    }
+
+    __device__ __forceinline__ void acc(int i, float2 y) { w[i] = __ffma2_rn(make_float2(y.x, y.x), y, w[i]); }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, uint32_t k0) {
+        const float C = B.y, S = B.z, C2 = B.w;
+        float s, c;
+        __sincosf(phase_to_angle(top_phase(A, k0)), &s, &c);
+        float2 y0 = make_float2(c, s);
+        acc(0, y0);
+        if (F == 1) return;
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, y1);
+        const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
+#pragma unroll
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            acc(i, y2);
+            y0 = y1;
+            y1 = y2;
+        }
+    }
+
+    __device__ __forceinline__ float get_cc(int i) const { return w[i].x; }
+    __device__ __forceinline__ float get_cs(int i) const { return w[i].y; }
 };
 
 // One 128-bit shared-memory load of a 16-byte record.  A float4 whose fourth
