@@ -32,9 +32,10 @@
 //             identity, z_{k+1} = 2 cos(2 pi u_j) z_k - z_{k-1}: 2 FMA-pipe ops
 //             per term.  Its rounding error grows like F^2 ulp, and like
 //             F ulp / sin(2 pi u_j) for samples whose step angle is near 0 or pi.
-//   RECUR3 x2 -- the same arithmetic in packed FP32x2 FMA (FFMA2), the two
-//             halves of the strip in the two lanes: half the issue slots per
-//             term; sums bit-identical to RECUR3 with strips of F/2.
+//   RECUR3 x2 -- the same arithmetic in packed FP32x2 FMA (FFMA2), the
+//             (cos, sin) pair of a frequency in the two lanes: (XC, XS),
+//             (CC, CS) and the step one FFMA2 each per term, half the issue
+//             slots; sums bit-identical to RECUR3 at the same F.  The default.
 // NAIVE_FP32 -- the paper's own single-precision phase f*t - rintf(f*t)
 //             (Sec. 4.3), kept as a comparator.
 #include "ls_device.cuh"
