@@ -170,6 +170,29 @@ lsp_status lsp_batch_gls(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, c
                          int32_t *argmax_out);
 
 /*
+ * Monte-Carlo noise periodograms in the floating-mean form (Sec. 6.2's
+ * Monte Carlo applied to the Sec. 6.3 extension): the statistics of its
+ * noise peaks depend on the errors as well as on the sampling pattern, so the
+ * noise carries them.  Realization r of curve c (r < n_real) is
+ * X_j = dy_j z_j with z_j the N(0,1) value that lsp_batch draws for
+ * (seed, c, r, j) (see lsp_noise; X_j = z_j when dy is NULL), and its
+ * periodogram is lsp_batch_gls's of that X with the same dy: weights 1/dy^2,
+ * the offset fitted.  Layout and outputs as lsp_batch with n_real
+ * realizations: P of realization r, curve c, bin k at
+ * P_out[r * P_off[n_curves] + P_off[c] + k] (optional); maxP_out, argmax_out
+ * [n_real * n_curves] at r * n_curves + c.  n_real in [1, 65535]; curves of at
+ * least 3 samples.  Runs the packed three-term strip (sin/cos mode AUTO or
+ * RECUR3_X2, strips of 16 or 8; other modes return UNSUPPORTED), one
+ * persistent launch over (curve, realization, frequency block) items.
+ * Pointers host or device; any host output makes the call blocking.
+ * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, OOM, CUDA.
+ */
+lsp_status lsp_batch_gls_noise(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, const double *t,
+                               const double *dy, uint64_t seed, int32_t n_real, const double *f_0,
+                               const double *df, const int64_t *N_f, float *P_out, const int64_t *P_off,
+                               float *maxP_out, int32_t *argmax_out);
+
+/*
  * Fast approximate P_n by the method of Press & Rybicki (1989), which the
  * paper's introduction cites as the O(N log N) alternative to the direct
  * evaluation: the normalized data are spread ("extirpolated") onto a uniform

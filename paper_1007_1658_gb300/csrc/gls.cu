@@ -249,12 +249,50 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsig
 // 99.0 ms) but halves each warp's own speed, so a batch whose longest curve
 // is a large share of the work (256 curves: 7.2 -> 8.2 ms) runs the unbounded
 // form; results are the same either way.
-template <int F, int MODE, int MINB>
+// With XROW the items are noise realizations (lsp_batch_gls_noise): item
+// (curve, realization r) takes its x from row r of xr (stride `total`) instead
+// of from the records, staged into the records' x slot as the tile arrives,
+// and writes P and the maximum of realization r (P at r P_total + P_off[c],
+// the key at r n_curves + c).  Measured curves are realization 0.
+template <int TILE, class Body>
+__device__ __forceinline__ void for_each_tile_gx(TileSmemN<1, TILE>& sm, const uint4* __restrict__ recA,
+                                                 const float4* __restrict__ recB, const float* __restrict__ q,
+                                                 const float* __restrict__ x, int64_t j0, int64_t j1,
+                                                 Body&& body) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntiles = j1 > j0 ? (int)((j1 - j0 + TILE - 1) / TILE) : 0;
+    auto stage = [&](int buf, int64_t jt) {
+        const int n = (int)min((int64_t)TILE, j1 - jt);
+        for (int i = tid; i < n; i += nt) {
+            cp_async16(&sm.A[buf][i], recA + jt + i);
+            float* dst = reinterpret_cast<float*>(&sm.B[buf][i]);
+            const float* src = reinterpret_cast<const float*>(recB + jt + i);
+            cp_async4(dst, x + jt + i);
+            cp_async4(dst + 1, src + 1);
+            cp_async8(dst + 2, src + 2);
+            cp_async4(&sm.X[buf][0][i], q + jt + i);
+        }
+    };
+    if (ntiles > 0) stage(0, j0);
+    cp_async_commit();
+    for (int it = 0; it < ntiles; ++it) {
+        const int64_t jt = j0 + (int64_t)it * TILE;
+        if (it + 1 < ntiles) stage((it + 1) & 1, jt + TILE);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        body(sm.A[it & 1], sm.B[it & 1], sm.X[it & 1], (int)min((int64_t)TILE, j1 - jt));
+        __syncthreads();
+    }
+}
+
+template <int F, int MODE, int MINB, bool XROW>
 __global__ void __launch_bounds__(kGlsBatchThreads, MINB)
 gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
                  const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
                  const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
-                 const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey) {
+                 const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey,
+                 const float* __restrict__ xr, int64_t total, int64_t P_total, int n_curves) {
     __shared__ __align__(16) TileSmemN<1, kGlsBatchTile> sm;
     __shared__ int s_item;
     __shared__ unsigned long long s_red[kGlsBatchThreads / 32];
@@ -271,16 +309,19 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         GStrip<F, MODE> st;
         st.zero();
         const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
-        for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e,
-                           [&](const uint4* a, const float4* bb, const float (*qs)[kGlsBatchTile], int n) {
-                               if (!live) return;
+        auto body = [&](const uint4* a, const float4* bb, const float (*qs)[kGlsBatchTile], int n) {
+            if (!live) return;
 #pragma unroll 2
-                               for (int j = 0; j < n; ++j) {
-                                   const float4 B = bb[j];
-                                   st.add(a[j], B, B.x, qs[0][j], k0);
-                               }
-                           });
-        float* P = P_out ? P_out + P_off[w.curve] : nullptr;
+            for (int j = 0; j < n; ++j) {
+                const float4 B = bb[j];
+                st.add(a[j], B, B.x, qs[0][j], k0);
+            }
+        };
+        if constexpr (XROW)
+            for_each_tile_gx(sm, recA, recB, q, xr + (size_t)w.real * (size_t)total, b, e, body);
+        else
+            for_each_tile_n<1>(sm, recA, recB, q, 0, 1, b, e, body);
+        float* P = P_out ? P_out + (size_t)w.real * (size_t)P_total + P_off[w.curve] : nullptr;
         unsigned long long best = 0ull;
 #pragma unroll
         for (int i = 0; i < F; ++i) {
@@ -297,31 +338,40 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
         if (threadIdx.x == 0) {
             unsigned long long m = s_red[0];
             for (int x = 1; x < kGlsBatchThreads / 32; ++x) m = umax64(m, s_red[x]);
-            if (m) atomicMax(&maxkey[w.curve], m);
+            if (m) atomicMax(&maxkey[(size_t)w.real * (size_t)n_curves + w.curve], m);
         }
     }
 }
 
 using GlsBatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const uint4*,
-                            const float4*, const float*, float*, const int64_t*, unsigned long long*);
+                            const float4*, const float*, float*, const int64_t*, unsigned long long*, const float*,
+                            int64_t, int64_t, int);
 
-GlsBatchFn gls_batch_fn(int mode, int F, bool packed) {
-    if (packed) return F == 16 && mode == kRecur3x2 ? gls_batch_kernel<16, kRecur3x2, 16> : nullptr;
+// Measured curves: every mode at F = 16 and 8, and the bounded packed form.
+// Noise realizations (xrow): the packed mode only, F = 16 (both forms) and 8.
+GlsBatchFn gls_batch_fn(int mode, int F, bool packed, bool xrow) {
+    if (xrow) {
+        if (mode != kRecur3x2) return nullptr;
+        if (packed) return F == 16 ? gls_batch_kernel<16, kRecur3x2, 16, true> : nullptr;
+        return F == 16 ? gls_batch_kernel<16, kRecur3x2, 1, true> : F == 8 ? gls_batch_kernel<8, kRecur3x2, 1, true>
+                                                                           : nullptr;
+    }
+    if (packed) return F == 16 && mode == kRecur3x2 ? gls_batch_kernel<16, kRecur3x2, 16, false> : nullptr;
     if (F == 16) {
         switch (mode) {
-            case kMufu: return gls_batch_kernel<16, kMufu, 1>;
-            case kRecur: return gls_batch_kernel<16, kRecur, 1>;
-            case kRecur3: return gls_batch_kernel<16, kRecur3, 1>;
-            case kRecur3x2: return gls_batch_kernel<16, kRecur3x2, 1>;
+            case kMufu: return gls_batch_kernel<16, kMufu, 1, false>;
+            case kRecur: return gls_batch_kernel<16, kRecur, 1, false>;
+            case kRecur3: return gls_batch_kernel<16, kRecur3, 1, false>;
+            case kRecur3x2: return gls_batch_kernel<16, kRecur3x2, 1, false>;
             default: return nullptr;
         }
     }
     if (F == 8) {
         switch (mode) {
-            case kMufu: return gls_batch_kernel<8, kMufu, 1>;
-            case kRecur: return gls_batch_kernel<8, kRecur, 1>;
-            case kRecur3: return gls_batch_kernel<8, kRecur3, 1>;
-            case kRecur3x2: return gls_batch_kernel<8, kRecur3x2, 1>;
+            case kMufu: return gls_batch_kernel<8, kMufu, 1, false>;
+            case kRecur: return gls_batch_kernel<8, kRecur, 1, false>;
+            case kRecur3: return gls_batch_kernel<8, kRecur3, 1, false>;
+            case kRecur3x2: return gls_batch_kernel<8, kRecur3x2, 1, false>;
             default: return nullptr;
         }
     }
@@ -373,8 +423,8 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
     return cudaGetLastError();
 }
 
-int gls_batch_occupancy(int mode, int F, bool packed) {
-    const GlsBatchFn fn = gls_batch_fn(mode, F, packed);
+int gls_batch_occupancy(int mode, int F, bool packed, bool xrow) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F, packed, xrow);
     if (!fn) return 0;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsBatchThreads, 0) != cudaSuccess) {
@@ -387,10 +437,12 @@ int gls_batch_occupancy(int mode, int F, bool packed) {
 cudaError_t launch_gls_batch(int mode, int F, bool packed, int grid, const BatchItem* items, int n_items,
                              unsigned* head, const int64_t* off, const int64_t* nf, const uint4* recA,
                              const float4* recB, const float* q, float* P_out, const int64_t* P_off,
-                             unsigned long long* maxkey, cudaStream_t st) {
-    const GlsBatchFn fn = gls_batch_fn(mode, F, packed);
+                             unsigned long long* maxkey, cudaStream_t st, const float* xr, int64_t total,
+                             int64_t P_total, int n_curves) {
+    const GlsBatchFn fn = gls_batch_fn(mode, F, packed, xr != nullptr);
     if (!fn) return cudaErrorInvalidValue;
-    fn<<<grid, kGlsBatchThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey);
+    fn<<<grid, kGlsBatchThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey, xr,
+                                          total, P_total, n_curves);
     return cudaGetLastError();
 }
 

@@ -381,7 +381,7 @@ void lsp_destroy(lsp_ctx* ctx) {
                       &ctx->b_recB,  &ctx->b_xr,   &ctx->b_stats, &ctx->b_items, &ctx->b_head, &ctx->b_maxkey,
                       &ctx->b_seed,  &ctx->b_off,  &ctx->b_nf,   &ctx->b_f0,    &ctx->b_df,   &ctx->b_poff,
                       &ctx->b_t,     &ctx->b_X,    &ctx->b_P,    &ctx->b_maxP,  &ctx->b_argmax,
-                      &ctx->b_win,   &ctx->b_woff};
+                      &ctx->b_win,   &ctx->b_woff, &ctx->b_gx};
     for (DevBuf* b : bufs)
         if (b->p) cudaFree(b->p);
     lsp::host::FapState& f = ctx->fap;

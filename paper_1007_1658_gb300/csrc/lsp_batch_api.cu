@@ -311,6 +311,11 @@ lsp_status lsp::host::batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t
     std::memcpy(ctx->pinned, &seed, sizeof seed);
     LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_seed.p, ctx->pinned, sizeof seed, cudaMemcpyHostToDevice, st));
     const bool timing = ctx->opt.timing != 0;
+    // a host P_out whose layout leaves slack between curves gets its own values
+    // staged first, so that the copy back returns the slack unchanged: the
+    // call writes only the bins, wherever P_out lives
+    if (P_out && !p_dev && p_layout_has_slack(poff, nf))
+        LSP_CUDA(ctx, cudaMemcpyAsync(d_P, P_out, (size_t)n_real * (size_t)P_total * 4, cudaMemcpyHostToDevice, st));
     if (timing) {
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
         LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));

@@ -93,7 +93,8 @@ struct lsp_ctx {
     // batch workspace
     lsp::host::DevBuf b_recA, b_recB, b_xr, b_stats, b_items, b_head, b_maxkey, b_seed, b_off, b_nf, b_f0,
         b_df, b_poff, b_t, b_X, b_P, b_maxP, b_argmax,
-        b_win, b_woff;  // multi-realization window sums (CC, CS) per frequency and their per-curve offsets
+        b_win, b_woff,  // multi-realization window sums (CC, CS) per frequency and their per-curve offsets
+        b_gx;           // floating-mean Monte Carlo: x of every realization
     void* pinned = nullptr;  // host staging for the work list and small values
     size_t pinned_cap = 0;
     lsp::host::BatchPlan plan;
@@ -246,6 +247,15 @@ inline lsp_status fetch(lsp_ctx* ctx, const T* src, size_t n, std::vector<T>& ds
         std::memcpy(dst.data(), src, n * sizeof(T));
     }
     return LSP_OK;
+}
+
+// True when a batch's P layout (P_off[0..n], N_f[0..n-1]) leaves slots that
+// no bin fills: before the first curve or after a curve's N_f bins.
+inline bool p_layout_has_slack(const std::vector<int64_t>& poff, const std::vector<int64_t>& nf) {
+    if (poff.empty() || poff[0] != 0) return true;
+    for (size_t c = 0; c < nf.size(); ++c)
+        if (poff[c + 1] - poff[c] != nf[c]) return true;
+    return false;
 }
 
 inline lsp_status ensure_pinned(lsp_ctx* ctx, size_t bytes) {

@@ -1,4 +1,4 @@
-// lsp_gls_api.cu -- lsp_periodogram_gls and lsp_batch_gls: the floating-mean
+// lsp_gls_api.cu -- lsp_periodogram_gls, lsp_batch_gls and lsp_batch_gls_noise: the floating-mean
 // (generalized, weighted) periodogram of one curve or of many (gls.cu).
 #include <algorithm>
 #include <cmath>
@@ -138,18 +138,24 @@ lsp_status lsp_periodogram_gls(lsp_ctx* ctx, const double* t, const double* X, c
 
 }  // extern "C"
 
-extern "C" {
+namespace {
 
-lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
-                         const double* dy, const double* f_0, const double* df, const int64_t* N_f, float* P_out,
-                         const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+// lsp_batch_gls (measured X, one realization) and lsp_batch_gls_noise (X =
+// NULL: n_real noise realizations drawn on the device) share this body; with
+// noise, item (curve, realization) takes its x from the realization's row.
+lsp_status gls_batch_run(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                         const double* dy, uint64_t seed, int32_t n_real, const double* f_0, const double* df,
+                         const int64_t* N_f, float* P_out, const int64_t* P_off, float* maxP_out,
+                         int32_t* argmax_out) {
     if (!ctx) return LSP_ERR_INVALID_ARG;
     ctx->err.clear();
     ctx->timing_valid = false;
     ctx->last_launches = 0;
     if (n_curves < 1 || n_curves > 65535)
         return fail(ctx, LSP_ERR_INVALID_ARG, "n_curves = %d out of range [1, 65535]", n_curves);
-    if (!t_off || !t || !X || !f_0 || !df || !N_f) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
+    if (n_real < 1 || n_real > 65535) return fail(ctx, LSP_ERR_INVALID_ARG, "n_real = %d out of range", n_real);
+    const bool noise = X == nullptr;
+    if (!t_off || !t || !f_0 || !df || !N_f) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
     if (!P_out && !maxP_out && !argmax_out) return fail(ctx, LSP_ERR_INVALID_ARG, "no output requested");
     if (P_out && !P_off) return fail(ctx, LSP_ERR_INVALID_ARG, "P_out needs P_off");
     if (ctx->opt.phase_mode != LSP_PHASE_FIXED64)
@@ -190,7 +196,7 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     if ((rs = device_view(ctx, df, (size_t)n_curves, ctx->b_df, &d_df)) != LSP_OK) return rs;
     if (P_out && (rs = device_view(ctx, P_off, (size_t)n_curves + 1, ctx->b_poff, &d_poff)) != LSP_OK) return rs;
     if ((rs = device_view(ctx, t, (size_t)total, ctx->b_t, &d_t)) != LSP_OK) return rs;
-    if ((rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
+    if (!noise && (rs = device_view(ctx, X, (size_t)total, ctx->b_X, &d_X)) != LSP_OK) return rs;
     if (dy && (rs = device_view(ctx, dy, (size_t)total, ctx->dy_stage, &d_dy)) != LSP_OK) return rs;
     bool p_dev = true, m_dev = true, a_dev = true;
     if (P_out && (rs = where(ctx, P_out, &p_dev)) != LSP_OK) return rs;
@@ -200,28 +206,35 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     // mode and strip length as for the single-curve floating-mean call
     const MainShape shape = choose_gls_shape(ctx, 1 << 20, 1 << 24);
     const int mode = shape.mode, F = shape.F;
+    if (noise && lsp::gls_batch_occupancy(mode, F, false, true) <= 0)
+        return fail(ctx, LSP_ERR_UNSUPPORTED, "noise realizations run the packed three-term strip of 16 or 8 "
+                                              "frequencies only (sin/cos mode AUTO or RECUR3_X2)");
     const int64_t per_block = lsp::gls_batch_freqs_per_block(F);
     std::vector<int> order(n_curves);
     for (int c = 0; c < n_curves; ++c) order[c] = c;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    // longest curve first, each curve's realizations together
     std::vector<lsp::BatchItem> items;
     for (int c : order) {
         const int64_t nfb = (nf[c] + per_block - 1) / per_block;
-        for (int64_t fb = 0; fb < nfb; ++fb) items.push_back({c, 0, (int32_t)fb, 1});
+        for (int r = 0; r < n_real; ++r)
+            for (int64_t fb = 0; fb < nfb; ++fb) items.push_back({c, r, (int32_t)fb, 1});
+        if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
     }
-    if (items.size() >= (size_t)(1u << 31)) return fail(ctx, LSP_ERR_INVALID_ARG, "batch too large");
+    const size_t n_out = (size_t)n_real * (size_t)n_curves;
 
     if ((rs = ensure(ctx, ctx->b_recA, (size_t)total * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->b_recB, (size_t)total * 16)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->b_xr, (size_t)total * 4)) != LSP_OK) return rs;  // the sqrt-weights
     if ((rs = ensure(ctx, ctx->b_stats, sizeof(lsp::CurveStats) * (size_t)n_curves)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->b_head, 16)) != LSP_OK) return rs;
-    if ((rs = ensure(ctx, ctx->b_maxkey, (size_t)n_curves * 8)) != LSP_OK) return rs;
+    if ((rs = ensure(ctx, ctx->b_maxkey, n_out * 8)) != LSP_OK) return rs;
+    if (noise && (rs = ensure(ctx, ctx->b_gx, (size_t)n_real * (size_t)total * 4)) != LSP_OK) return rs;
     if ((rs = ensure(ctx, ctx->b_items, items.size() * sizeof(lsp::BatchItem) + 16)) != LSP_OK) return rs;
-    if (!p_dev && (rs = ensure(ctx, ctx->b_P, (size_t)P_total * 4)) != LSP_OK) return rs;
-    if (!m_dev && (rs = ensure(ctx, ctx->b_maxP, (size_t)n_curves * 4)) != LSP_OK) return rs;
-    if (!a_dev && (rs = ensure(ctx, ctx->b_argmax, (size_t)n_curves * 4)) != LSP_OK) return rs;
+    if (!p_dev && (rs = ensure(ctx, ctx->b_P, (size_t)n_real * (size_t)P_total * 4)) != LSP_OK) return rs;
+    if (!m_dev && (rs = ensure(ctx, ctx->b_maxP, n_out * 4)) != LSP_OK) return rs;
+    if (!a_dev && (rs = ensure(ctx, ctx->b_argmax, n_out * 4)) != LSP_OK) return rs;
     float* d_P = P_out ? (p_dev ? P_out : (float*)ctx->b_P.p) : nullptr;
     float* d_maxP = maxP_out ? (m_dev ? maxP_out : (float*)ctx->b_maxP.p) : nullptr;
     int32_t* d_argmax = argmax_out ? (a_dev ? argmax_out : (int32_t*)ctx->b_argmax.p) : nullptr;
@@ -233,10 +246,14 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
         std::memcpy(ctx->pinned, items.data(), item_bytes);
         LSP_CUDA(ctx, cudaMemcpyAsync(ctx->b_items.p, ctx->pinned, item_bytes, cudaMemcpyHostToDevice, st));
     }
+    // a host P_out whose layout leaves slack between curves gets its own values
+    // staged first, so that the copy back returns the slack unchanged
+    if (P_out && !p_dev && p_layout_has_slack(poff, nf))
+        LSP_CUDA(ctx, cudaMemcpyAsync(d_P, P_out, (size_t)n_real * (size_t)P_total * 4, cudaMemcpyHostToDevice, st));
     const bool timing = ctx->opt.timing != 0;
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[0], st));
     LSP_CUDA(ctx, cudaMemsetAsync(ctx->b_head.p, 0, 16, st));
-    LSP_CUDA(ctx, cudaMemsetAsync(ctx->b_maxkey.p, 0, (size_t)n_curves * 8, st));
+    LSP_CUDA(ctx, cudaMemsetAsync(ctx->b_maxkey.p, 0, n_out * 8, st));
     lsp::CurveStats* stats = (lsp::CurveStats*)ctx->b_stats.p;
     LSP_CUDA(ctx, lsp::launch_prep_stats(d_t, d_X, d_off, 0, n_curves, stats, ctx->status_d, nullptr, nullptr, st,
                                          d_dy));
@@ -244,8 +261,13 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     LSP_CUDA(ctx, lsp::launch_prep_records(d_t, d_X, d_off, 0, n_curves, max_n, d_f0, d_df, 0.0, 0.0, stats,
                                            (uint4*)ctx->b_recA.p, (float4*)ctx->b_recB.p, nullptr, nullptr, st,
                                            d_dy, (float*)ctx->b_xr.p, ctx->status_d));
-    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     int launches = 2;
+    if (noise) {
+        LSP_CUDA(ctx, lsp::launch_gls_noise_prep(d_off, n_curves, n_real, seed, total, d_dy, (const float*)ctx->b_xr.p,
+                                                 (float*)ctx->b_gx.p, st));
+        ++launches;
+    }
+    if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[1], st));
     if (!items.empty()) {
         NvtxRange r("lsp_batch_gls.main");
         // the packed form when the work is many times the longest curve's, per
@@ -255,21 +277,24 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
         double work = 0.0;
         for (int c = 0; c < n_curves; ++c)
             work += (double)(off[c + 1] - off[c]) * (double)((nf[c] + per_block - 1) / per_block);
-        const bool packed = lsp::gls_batch_occupancy(mode, F, true) > 0 &&
+        work *= (double)n_real;
+        const bool packed = lsp::gls_batch_occupancy(mode, F, true, noise) > 0 &&
                             work >= 12.0 * 4.0 * ctx->sms * (double)max_n;
-        const int occ = std::max(1, lsp::gls_batch_occupancy(mode, F, packed));
+        const int occ = std::max(1, lsp::gls_batch_occupancy(mode, F, packed, noise));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)occ * ctx->sms, (int64_t)items.size()));
         LSP_CUDA(ctx, lsp::launch_gls_batch(mode, F, packed, grid, (const lsp::BatchItem*)ctx->b_items.p,
                                             (int)items.size(),
                                             (unsigned*)ctx->b_head.p, d_off, d_nf, (const uint4*)ctx->b_recA.p,
                                             (const float4*)ctx->b_recB.p, (const float*)ctx->b_xr.p, d_P, d_poff,
-                                            (unsigned long long*)ctx->b_maxkey.p, st));
+                                            (unsigned long long*)ctx->b_maxkey.p, st,
+                                            noise ? (const float*)ctx->b_gx.p : nullptr, total, P_total,
+                                            n_curves));
         ++launches;
     }
     if (timing) LSP_CUDA(ctx, cudaEventRecord(ctx->ev[2], st));
     if (d_maxP || d_argmax) {
-        LSP_CUDA(ctx, lsp::launch_unpack_max((const unsigned long long*)ctx->b_maxkey.p, n_curves, d_maxP, d_argmax,
-                                             st));
+        LSP_CUDA(ctx, lsp::launch_unpack_max((const unsigned long long*)ctx->b_maxkey.p, (int64_t)n_out, d_maxP,
+                                             d_argmax, st));
         ++launches;
     }
     if (timing) {
@@ -280,19 +305,38 @@ lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, c
     ctx->last_launches = launches;
     bool host_out = false;
     if (P_out && !p_dev) {
-        LSP_CUDA(ctx, cudaMemcpyAsync(P_out, d_P, (size_t)P_total * 4, cudaMemcpyDeviceToHost, st));
+        LSP_CUDA(ctx, cudaMemcpyAsync(P_out, d_P, (size_t)n_real * (size_t)P_total * 4, cudaMemcpyDeviceToHost, st));
         host_out = true;
     }
     if (maxP_out && !m_dev) {
-        LSP_CUDA(ctx, cudaMemcpyAsync(maxP_out, d_maxP, (size_t)n_curves * 4, cudaMemcpyDeviceToHost, st));
+        LSP_CUDA(ctx, cudaMemcpyAsync(maxP_out, d_maxP, n_out * 4, cudaMemcpyDeviceToHost, st));
         host_out = true;
     }
     if (argmax_out && !a_dev) {
-        LSP_CUDA(ctx, cudaMemcpyAsync(argmax_out, d_argmax, (size_t)n_curves * 4, cudaMemcpyDeviceToHost, st));
+        LSP_CUDA(ctx, cudaMemcpyAsync(argmax_out, d_argmax, n_out * 4, cudaMemcpyDeviceToHost, st));
         host_out = true;
     }
     if (host_out) return lsp_sync(ctx, -1.0);
     return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsp_status lsp_batch_gls(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t, const double* X,
+                         const double* dy, const double* f_0, const double* df, const int64_t* N_f, float* P_out,
+                         const int64_t* P_off, float* maxP_out, int32_t* argmax_out) {
+    if (ctx && !X) return fail(ctx, LSP_ERR_INVALID_ARG, "null array pointer");
+    return gls_batch_run(ctx, n_curves, t_off, t, X, dy, 0, 1, f_0, df, N_f, P_out, P_off, maxP_out, argmax_out);
+}
+
+lsp_status lsp_batch_gls_noise(lsp_ctx* ctx, int32_t n_curves, const int64_t* t_off, const double* t,
+                               const double* dy, uint64_t seed, int32_t n_real, const double* f_0, const double* df,
+                               const int64_t* N_f, float* P_out, const int64_t* P_off, float* maxP_out,
+                               int32_t* argmax_out) {
+    return gls_batch_run(ctx, n_curves, t_off, t, nullptr, dy, seed, n_real, f_0, df, N_f, P_out, P_off, maxP_out,
+                         argmax_out);
 }
 
 }  // extern "C"

@@ -141,11 +141,24 @@ struct BatchItem;
 // Many curves (CSR samples, per-curve grids) in one persistent launch; F in {8, 16}.
 // packed: the form held to 16 CTAs per SM (built for F = 16, RECUR3 x2), for
 // batches whose work is many times their longest curve's.
-int gls_batch_occupancy(int mode, int F, bool packed = false);
+// xr (noise realizations, RECUR3 x2 only): item (curve c, realization r) takes
+// x from xr[r total + j] instead of the records, and writes P at
+// P_out[r P_total + P_off[c] + k] and its maximum at maxkey[r n_curves + c];
+// without xr every item is realization 0.
+int gls_batch_occupancy(int mode, int F, bool packed = false, bool xrow = false);
 cudaError_t launch_gls_batch(int mode, int F, bool packed, int grid, const BatchItem* items, int n_items,
                              unsigned* head, const int64_t* off, const int64_t* nf, const uint4* recA,
                              const float4* recB, const float* q, float* P_out, const int64_t* P_off,
-                             unsigned long long* maxkey, cudaStream_t st);
+                             unsigned long long* maxkey, cudaStream_t st, const float* xr = nullptr,
+                             int64_t total = 0, int64_t P_total = 0, int n_curves = 0);
+// Noise for the floating-mean Monte Carlo: realization r of curve c is
+// X_j = dy_j z_j (z_j the N(0,1) value of lsp_batch's generator for (seed, c,
+// r, j); X = z without dy), normalized as prep_records does for measured
+// curves: x_j = q_j (X_j - mean_w) / sd_w with the weights 1/dy^2 (FP64 mean
+// and population variance), q_j = sqrt(w_j) as launch_prep_records wrote it.
+// Row r of xr (stride `total`) receives x.
+cudaError_t launch_gls_noise_prep(const int64_t* off, int n_curves, int n_real, uint64_t seed, int64_t total,
+                                  const double* dy, const float* q, float* xr, cudaStream_t st);
 
 // ---- Press-Rybicki fast approximation (press_rybicki.cu) ----
 

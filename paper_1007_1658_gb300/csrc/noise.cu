@@ -104,7 +104,63 @@ noise_prep_kernel(const int64_t* __restrict__ off, const uint64_t* __restrict__ 
     }
 }
 
+// One CTA per (curve, realization) of the floating-mean Monte Carlo: the
+// same N(0,1) draws z_j as noise_prep_kernel, X_j = dy_j z_j (z_j without dy),
+// then the weighted normalization of prep_records_kernel's floating-mean form,
+// x_j = q_j (X_j - mean_w) / sd_w, with v_j = 1/dy_j^2 formed in FP32 as the
+// prep kernels form it, mean_w = sum v X / sum v and the population variance
+// sum v (X - mean_w)^2 / sum v in FP64.  X_j is re-formed from the stored z_j
+// in every pass (exact: a float times a double).
+__global__ void __launch_bounds__(kNoiseThreads)
+gls_noise_prep_kernel(const int64_t* __restrict__ off, uint64_t seed, int64_t total, const double* __restrict__ dy,
+                      const float* __restrict__ q, float* __restrict__ xr) {
+    __shared__ double sh[33];
+    const int c = blockIdx.x, r = blockIdx.y;
+    const int64_t b = off[c], n = off[c + 1] - off[c];
+    float* x = xr + (size_t)r * (size_t)total + b;
+    auto weight = [&](int64_t j) {
+        if (!dy) return 1.0;
+        const float ef = (float)dy[b + j];
+        return (double)(1.f / (ef * ef));
+    };
+    auto value = [&](int64_t j) { return dy ? dy[b + j] * (double)x[j] : (double)x[j]; };
+    double sv = 0.0, svx = 0.0;
+    for (int64_t blk = threadIdx.x; blk * 4 < n; blk += blockDim.x) {
+        const float4 z = normals4(seed, (uint32_t)blk, (uint32_t)c, (uint32_t)r);
+        const int64_t j = blk * 4;
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (j + u < n) {
+                x[j + u] = zz[u];
+                const double v = weight(j + u);
+                sv += v;
+                svx += v * value(j + u);
+            }
+        }
+    }
+    __syncthreads();
+    sv = block_sum(sv, sh);
+    const double mean = block_sum(svx, sh) / sv;
+    double m2 = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double d = value(j) - mean;
+        m2 = fma(d * weight(j), d, m2);
+    }
+    const double var = block_sum(m2, sh) / sv;
+    const double inv_sd = var > 0.0 ? 1.0 / sqrt(var) : 0.0;
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) x[j] = (float)((value(j) - mean) * inv_sd) * q[b + j];
+}
+
 }  // namespace
+
+cudaError_t launch_gls_noise_prep(const int64_t* off, int n_curves, int n_real, uint64_t seed, int64_t total,
+                                  const double* dy, const float* q, float* xr, cudaStream_t st) {
+    dim3 grid((unsigned)n_curves, (unsigned)n_real);
+    gls_noise_prep_kernel<<<grid, kNoiseThreads, 0, st>>>(off, seed, total, dy, q, xr);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_noise_raw(uint64_t seed, uint32_t curve, uint32_t real, int64_t n, float* out, cudaStream_t st) {
     const int64_t nb = (n + 3) / 4;

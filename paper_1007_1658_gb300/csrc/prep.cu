@@ -252,7 +252,8 @@ prep_records_kernel(const double* __restrict__ t, const double* __restrict__ X,
             // equal weights without dy), x = q (X - mean_w) / sd_w, so sum x^2 = 1
             const float q = dy ? isw / (float)dy[j] : isw;
             qout[j] = q;
-            xh = (float)((X[j] - st.mean) * st.inv_sd) * q;
+            // without X (noise realizations, normalized later per realization) x_hat = 0
+            xh = X ? (float)((X[j] - st.mean) * st.inv_sd) * q : 0.f;
         } else {
             xh = X ? (float)((X[j] - st.mean) * st.inv_sd) : 0.f;
         }

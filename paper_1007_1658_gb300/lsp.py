@@ -109,6 +109,9 @@ def _extra_prototypes(lib):
     if hasattr(lib, "lsp_batch"):
         lib.lsp_batch.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
         lib.lsp_batch.restype = ctypes.c_int
+    if hasattr(lib, "lsp_batch_gls_noise"):
+        lib.lsp_batch_gls_noise.argtypes = [p, i32, p, p, p, u64, i32, p, p, p, p, p, p, p]
+        lib.lsp_batch_gls_noise.restype = ctypes.c_int
     if hasattr(lib, "lsp_fap_features"):
         lib.lsp_fap_features.argtypes = [p, i32, p, p, p, p, p, p]
         lib.lsp_fap_init.argtypes = [p, i32, u64, i32, p]
@@ -278,6 +281,21 @@ class Context:
         self._bind_stream()
         self._check(self._lib.lsp_batch_gls(self.h, n, _ptr(t_off), _ptr(t), _ptr(X), _ptr(dy), _ptr(f0), _ptr(df),
                                             _ptr(nf), _ptr(P_out), _ptr(P_off), _ptr(maxP), _ptr(argmax)))
+        return maxP, argmax
+
+    def batch_gls_noise(self, t_off, t, f0, df, nf, dy=None, seed=0, n_real=1, P_out=None, P_off=None,
+                        maxP=None, argmax=None):
+        """lsp_batch_gls_noise: n_real floating-mean noise periodograms per curve
+        (X = dy z, z the Philox N(0,1) values of lsp_batch).  A missing maxP/argmax
+        is allocated like t and returned."""
+        n = int(nf.numel() if hasattr(nf, "numel") else len(nf))
+        if maxP is None and argmax is None and P_out is None:
+            maxP = _like(t, (n_real * n,), np.float32)
+            argmax = _like(t, (n_real * n,), np.int32)
+        self._bind_stream()
+        self._check(self._lib.lsp_batch_gls_noise(self.h, n, _ptr(t_off), _ptr(t), _ptr(dy), ctypes.c_uint64(int(seed)),
+                                                  int(n_real), _ptr(f0), _ptr(df), _ptr(nf), _ptr(P_out),
+                                                  _ptr(P_off), _ptr(maxP), _ptr(argmax)))
         return maxP, argmax
 
     def batch(self, t_off, t, f0, df, nf, X=None, seed=0, n_real=1, P_out=None, P_off=None,

@@ -138,6 +138,38 @@ def test_batch_writes_only_its_bins(lsp, n_real, rhs):
     ctx.close()
 
 
+@pytest.mark.parametrize("n_real", [1, 13])
+def test_batch_host_output_keeps_its_slack(lsp, n_real):
+    """A host P_out is staged through device memory; the slack its layout
+    leaves between curves must come back as the caller left it."""
+    b, P_off = _batch_with_slack(n_curves=7, seed=23)
+    n = n_real * int(P_off[-1])
+    buf = np.full(n + 2 * PAD, CANARY, dtype=np.int32)
+    P = buf.view(np.float32)[PAD:PAD + n]
+    ctx = lsp.Context(0)
+    ctx.batch(b.t_off, b.t, b.f0, b.df, b.nf, seed=5, n_real=n_real, P_out=P, P_off=P_off,
+              maxP=np.empty(n_real * b.n, np.float32), argmax=np.empty(n_real * b.n, np.int32))
+    assert np.all(buf[:PAD] == CANARY) and np.all(buf[PAD + n:] == CANARY)
+    assert _slack_intact(buf[PAD:PAD + n], b, P_off, n_real)
+    ctx.close()
+
+
+def test_floating_mean_batch_host_output_keeps_its_slack(lsp):
+    b, P_off = _batch_with_slack(n_curves=7, seed=24)
+    rng = np.random.default_rng(24)
+    X = rng.normal(size=b.t.size)
+    dy = rng.uniform(0.5, 2.0, b.t.size)
+    n = int(P_off[-1])
+    buf = np.full(n + 2 * PAD, CANARY, dtype=np.int32)
+    P = buf.view(np.float32)[PAD:PAD + n]
+    ctx = lsp.Context(0)
+    ctx.batch_gls(b.t_off, b.t, X, b.f0, b.df, b.nf, dy=dy, P_out=P, P_off=P_off,
+                  maxP=np.empty(b.n, np.float32), argmax=np.empty(b.n, np.int32))
+    assert np.all(buf[:PAD] == CANARY) and np.all(buf[PAD + n:] == CANARY)
+    assert _slack_intact(buf[PAD:PAD + n], b, P_off, 1)
+    ctx.close()
+
+
 def test_floating_mean_batch_writes_only_its_bins(lsp):
     b, P_off = _batch_with_slack(seed=22)
     rng = np.random.default_rng(4)
