@@ -540,9 +540,22 @@ def run_gls_bench(torch, dev, stream, args, peaks, peak_src, sms):
     dy_b = d(bdy)
     bfn = lambda: bctx.batch_gls(*bargs, dy=dy_b, maxP=bmax, argmax=barg)
     b_ms = _time_calls(torch, stream, bfn, 2, 3, flush)
-    bctx.close()
     batch_line = {"workload": "%d noise_batch patterns as measured curves with errors, N_f = 2 N_t" % b.n,
                   "ms": b_ms, "curves_per_s": b.n / (b_ms * 1e-3), "terms_per_s": b.terms / (b_ms * 1e-3)}
+    # Monte Carlo of the floating-mean form: noise realizations X = dy z drawn on the device
+    nb = synth.noise_batch(n_curves=256, seed=777001)
+    ndy = d(np.exp(np.random.default_rng(18).uniform(np.log(0.3), np.log(3.0), nb.t.size)))
+    n_real = 16
+    nargs = (d(nb.t_off), d(nb.t), d(nb.f0), d(nb.df), d(nb.nf))
+    nmax = torch.empty(n_real * nb.n, dtype=torch.float32, device=dev)
+    narg = torch.empty(n_real * nb.n, dtype=torch.int32, device=dev)
+    nfn = lambda: bctx.batch_gls_noise(*nargs, dy=ndy, seed=3, n_real=n_real, maxP=nmax, argmax=narg)
+    n_ms = _time_calls(torch, stream, nfn, 2, 3, flush)
+    bctx.close()
+    batch_line["noise_mc"] = {"workload": "%d noise_batch patterns x %d realizations with errors (X = dy z)"
+                                          % (nb.n, n_real),
+                              "ms": n_ms, "periodograms_per_s": n_real * nb.n / (n_ms * 1e-3),
+                              "terms_per_s": n_real * nb.terms / (n_ms * 1e-3)}
     return {"workload": "gapped_100k with per-sample errors (dy log-U[0.15, 1.5], 2%% x10), N_t = %d, N_f = %d"
                         % (c.t.size, c.nf),
             "batch": batch_line,
