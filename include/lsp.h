@@ -181,9 +181,16 @@ lsp_status lsp_batch_gls(lsp_ctx *ctx, int32_t n_curves, const int64_t *t_off, c
  * realizations: P of realization r, curve c, bin k at
  * P_out[r * P_off[n_curves] + P_off[c] + k] (optional); maxP_out, argmax_out
  * [n_real * n_curves] at r * n_curves + c.  n_real in [1, 65535]; curves of at
- * least 3 samples.  Runs the packed three-term strip (sin/cos mode AUTO or
- * RECUR3_X2, strips of 16 or 8; other modes return UNSUPPORTED), one
- * persistent launch over (curve, realization, frequency block) items.
+ * least 3 samples.  Groups of R realizations (the batch_rhs option; auto: 8
+ * from 8 realizations on, else 4; 1 = one at a time) share each pass over a
+ * curve's samples: the phase, the recurrence and the sums of the sampling
+ * pattern and weights are computed once for the group, only XC, XS per
+ * realization (strips of 8 frequencies for R = 2, 4, of 4 for R = 8; one at a
+ * time, strips of 16 or 8), one persistent launch over (curve, group,
+ * frequency block) items; each (frequency, realization) is computed exactly
+ * as the one-at-a-time kernel with the same strip length would.  Runs the
+ * packed three-term strip (sin/cos mode AUTO or RECUR3_X2; other modes return
+ * UNSUPPORTED).
  * Pointers host or device; any host output makes the call blocking.
  * Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, OOM, CUDA.
  */

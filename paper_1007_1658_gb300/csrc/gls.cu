@@ -343,6 +343,178 @@ gls_batch_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __r
     }
 }
 
+// Floating-mean strip for R noise realizations of one curve (packed form):
+// the realizations share the phase, the (cos, sin) recurrence and the sums
+// of the sampling pattern and weights, (C, S) and (CC', CS'); each keeps its
+// own (XC, XS).  Every operation is an FFMA2 with the (cos, sin) pair y in
+// the lanes, signs g_i folded into the sums as in the other packed strips:
+// per term and realization 2 lane operations plus 6 / R for the shared ones,
+// against 8 one at a time.  Each (frequency, realization) comes out bit for
+// bit as GStrip<F, kRecur3x2> computes it.
+template <int F, int R>
+struct GMStrip {
+    float2 a[F][R];  // g_i (XC, XS) of realization r
+    float2 w1[F];    // g_i (C, S)
+    float2 w2[F];    // (CC', CS')
+
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < F; ++i) {
+            w1[i] = w2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[i][r] = make_float2(0.f, 0.f);
+        }
+    }
+
+    __device__ __forceinline__ float value(int i, int r, double n) const {
+        const float g = ((i >> 1) & 1) ? -1.f : 1.f;
+        return gls_value(g * a[i][r].x, g * a[i][r].y, g * w1[i].x, g * w1[i].y, w2[i].x, w2[i].y, n);
+    }
+
+    __device__ __forceinline__ void acc(int i, const float2 (&xp)[R], float2 qp, float2 y) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[i][r] = __ffma2_rn(xp[r], y, a[i][r]);
+        w1[i] = __ffma2_rn(qp, y, w1[i]);
+        w2[i] = __ffma2_rn(make_float2(y.x, y.x), y, w2[i]);
+    }
+
+    __device__ __forceinline__ void add(const uint4& A, const float4& B, const float (&x)[R], float q, uint32_t k0) {
+        const uint32_t p = top_phase_hi(A, k0);
+        const float C = B.y, S = B.z, C2 = B.w;
+        float s, c;
+        __sincosf(phase_to_angle(p), &s, &c);
+        c *= q;
+        s *= q;
+        float2 xp[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) xp[r] = make_float2(x[r], x[r]);
+        const float2 qp = make_float2(q, q);
+        const float2 cp2 = make_float2(C2, C2), cn2 = make_float2(-C2, -C2);
+        float2 y0 = make_float2(c, s);
+        acc(0, xp, qp, y0);
+        if (F == 1) return;
+        float2 y1 = make_float2(fmaf(c, C, -s * S), fmaf(s, C, c * S));
+        acc(1, xp, qp, y1);
+#pragma unroll
+        for (int i = 2; i < F; ++i) {
+            const float2 y2 = __ffma2_rn(((i - 1) & 1) ? cn2 : cp2, y1, y0);
+            acc(i, xp, qp, y2);
+            y0 = y1;
+            y1 = y2;
+        }
+    }
+};
+
+// Tile of the floating-mean realization groups: the two records, the R
+// realizations' x of a sample side by side (one 128-bit load for R = 4) and
+// the sqrt-weight q.
+template <int R, int TILE>
+struct GTileX {
+    uint4 A[2][TILE];
+    float4 B[2][TILE];
+    float X[2][TILE][R];
+    float Q[2][TILE];
+};
+
+// Persistent kernel over (curve, group of up to R realizations starting at
+// w.real, frequency block) items (w.pad = the group's size) of a floating-mean
+// Monte Carlo: x of realization r from row r of xr (stride `total`), P of
+// realization r at P_out[r P_total + P_off[c] + k], its maximum at
+// maxkey[r n_curves + c].
+template <int F, int R, int TILE>
+__global__ void __launch_bounds__(kGlsBatchThreads)
+gls_mrhs_kernel(const BatchItem* __restrict__ items, int n_items, unsigned* __restrict__ head,
+                const int64_t* __restrict__ off, const int64_t* __restrict__ nf, const uint4* __restrict__ recA,
+                const float4* __restrict__ recB, const float* __restrict__ q, float* __restrict__ P_out,
+                const int64_t* __restrict__ P_off, unsigned long long* __restrict__ maxkey,
+                const float* __restrict__ xr, int64_t total, int64_t P_total, int n_curves) {
+    __shared__ __align__(16) GTileX<R, TILE> sm;
+    __shared__ int s_item;
+    static_assert(kGlsBatchThreads == 32, "the maxima are reduced within one warp");
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(head, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const int64_t b = off[w.curve], e = off[w.curve + 1];
+        const int64_t N_f = nf[w.curve];
+        const int nr = w.pad;
+        const uint32_t k0 = (uint32_t)w.fblock * (kGlsBatchThreads * F) + (uint32_t)threadIdx.x * F;
+        GMStrip<F, R> st;
+        st.zero();
+        const bool live = k0 < (uint32_t)N_f;  // padding strips only help stage the tiles
+        const float* x0 = xr + (size_t)w.real * (size_t)total;
+        const int ntiles = e > b ? (int)((e - b + TILE - 1) / TILE) : 0;
+        auto stage = [&](int buf, int64_t jt) {
+            const int n = (int)min((int64_t)TILE, e - jt);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                cp_async16(&sm.A[buf][i], recA + jt + i);
+                cp_async16(&sm.B[buf][i], recB + jt + i);
+                cp_async4(&sm.Q[buf][i], q + jt + i);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r < nr)
+                        cp_async4(&sm.X[buf][i][r], x0 + (size_t)r * (size_t)total + jt + i);
+                    else
+                        sm.X[buf][i][r] = 0.f;  // missing realizations of the last group add nothing
+                }
+            }
+        };
+        if (ntiles > 0) stage(0, b);
+        cp_async_commit();
+        for (int t = 0; t < ntiles; ++t) {
+            const int64_t jt = b + (int64_t)t * TILE;
+            if (t + 1 < ntiles) stage((t + 1) & 1, jt + TILE);
+            cp_async_commit();
+            cp_async_wait1();
+            __syncthreads();
+            const int n = (int)min((int64_t)TILE, e - jt);
+            if (live) {
+                const int bf = t & 1;
+#pragma unroll 2
+                for (int j = 0; j < n; ++j) {
+                    float x[R];
+                    if constexpr (R % 4 == 0) {
+#pragma unroll
+                        for (int u = 0; u < R / 4; ++u) {
+                            const float4 v = reinterpret_cast<const float4*>(sm.X[bf][j])[u];
+                            x[4 * u] = v.x;
+                            x[4 * u + 1] = v.y;
+                            x[4 * u + 2] = v.z;
+                            x[4 * u + 3] = v.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < R; ++r) x[r] = sm.X[bf][j][r];
+                    }
+                    st.add(sm.A[bf][j], sm.B[bf][j], x, sm.Q[bf][j], k0);
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r >= nr) break;
+            float* P = P_out ? P_out + (size_t)(w.real + r) * (size_t)P_total + P_off[w.curve] : nullptr;
+            unsigned long long best = 0ull;
+#pragma unroll
+            for (int i = 0; i < F; ++i) {
+                const uint32_t k = k0 + i;
+                if (k < (uint32_t)N_f) {
+                    const float p = st.value(i, r, (double)(e - b));
+                    if (P) P[k] = p;
+                    best = umax64(best, ((unsigned long long)__float_as_uint(p) << 32) | (unsigned long long)(~k));
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) best = umax64(best, __shfl_down_sync(0xffffffffu, best, o));
+            if (threadIdx.x == 0 && best)
+                atomicMax(&maxkey[(size_t)(w.real + r) * (size_t)n_curves + w.curve], best);
+        }
+    }
+}
+
 using GlsBatchFn = void (*)(const BatchItem*, int, unsigned*, const int64_t*, const int64_t*, const uint4*,
                             const float4*, const float*, float*, const int64_t*, unsigned long long*, const float*,
                             int64_t, int64_t, int);
@@ -420,6 +592,37 @@ cudaError_t launch_gls(const MainShape& s, const uint4* recA, const float4* recB
     dim3 grid((unsigned)s.nfb, (unsigned)s.split);
     fn<<<grid, kGlsThreads, 0, st>>>(recA, recB, q, N, s.chunk, (int)N_f, s.nf_pad, part,
                                       s.split == 1 ? P_out : nullptr);
+    return cudaGetLastError();
+}
+
+using GlsMrhsFn = GlsBatchFn;
+
+GlsMrhsFn gls_mrhs_fn(int F, int R) {
+    if (F == 8 && R == 4) return gls_mrhs_kernel<8, 4, kGlsBatchTile>;
+    if (F == 4 && R == 8) return gls_mrhs_kernel<4, 8, 64>;
+    if (F == 8 && R == 2) return gls_mrhs_kernel<8, 2, kGlsBatchTile>;
+    return nullptr;
+}
+
+int gls_mrhs_occupancy(int F, int R) {
+    const GlsMrhsFn fn = gls_mrhs_fn(F, R);
+    if (!fn) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)fn, kGlsBatchThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_gls_mrhs(int F, int R, int grid, const BatchItem* items, int n_items, unsigned* head,
+                            const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
+                            const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
+                            const float* xr, int64_t total, int64_t P_total, int n_curves, cudaStream_t st) {
+    const GlsMrhsFn fn = gls_mrhs_fn(F, R);
+    if (!fn || !xr) return cudaErrorInvalidValue;
+    fn<<<grid, kGlsBatchThreads, 0, st>>>(items, n_items, head, off, nf, recA, recB, q, P_out, P_off, maxkey, xr,
+                                          total, P_total, n_curves);
     return cudaGetLastError();
 }
 

@@ -151,6 +151,15 @@ cudaError_t launch_gls_batch(int mode, int F, bool packed, int grid, const Batch
                              const float4* recB, const float* q, float* P_out, const int64_t* P_off,
                              unsigned long long* maxkey, cudaStream_t st, const float* xr = nullptr,
                              int64_t total = 0, int64_t P_total = 0, int n_curves = 0);
+// Realization groups of the floating-mean Monte Carlo (RECUR3 x2): items are
+// (curve, up to R realizations from w.real, frequency block) with w.pad the
+// group's size; the group shares the phase, the recurrence and the pattern
+// sums.  (F, R) in {(8, 4), (4, 8), (8, 2)}.  Outputs as launch_gls_batch with xr.
+int gls_mrhs_occupancy(int F, int R);
+cudaError_t launch_gls_mrhs(int F, int R, int grid, const BatchItem* items, int n_items, unsigned* head,
+                            const int64_t* off, const int64_t* nf, const uint4* recA, const float4* recB,
+                            const float* q, float* P_out, const int64_t* P_off, unsigned long long* maxkey,
+                            const float* xr, int64_t total, int64_t P_total, int n_curves, cudaStream_t st);
 // Noise for the floating-mean Monte Carlo: realization r of curve c is
 // X_j = dy_j z_j (z_j the N(0,1) value of lsp_batch's generator for (seed, c,
 // r, j); X = z without dy), normalized as prep_records does for measured

@@ -128,3 +128,48 @@ def test_refusals(lsp):
     mx, am = ctx.batch_gls_noise(b.t_off, b.t, b.f0, b.df, b.nf, dy=dy, n_real=2)
     assert np.all(np.isfinite(mx)) and np.all(am >= 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("R", [2, 4])
+def test_realization_groups_match_one_at_a_time(lsp, R):
+    """Groups of R realizations share the phase, the recurrence and the
+    pattern sums; every (frequency, realization) must come out bit for bit as
+    the one-at-a-time kernel with the same strip length (8) computes it, with a
+    partial last group."""
+    b, dy = _batch(n_curves=5, seed=61)
+    n_real = 2 * R + 1
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    outs = []
+    for rhs in (1, R):
+        ctx = lsp.Context(0, batch_rhs=rhs, freqs_per_thread=8)
+        P = np.empty(n_real * int(P_off[-1]), np.float32)
+        mx = np.empty(n_real * b.n, np.float32)
+        am = np.empty(n_real * b.n, np.int32)
+        ctx.batch_gls_noise(b.t_off, b.t, b.f0, b.df, b.nf, dy=dy, seed=8, n_real=n_real, P_out=P, P_off=P_off,
+                            maxP=mx, argmax=am)
+        outs.append((P, mx, am))
+        ctx.close()
+    assert np.array_equal(outs[0][0].view(np.uint32), outs[1][0].view(np.uint32))
+    assert np.array_equal(outs[0][1].view(np.uint32), outs[1][1].view(np.uint32))
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
+def test_groups_of_eight_match_the_oracle(lsp):
+    b, dy = _batch(n_curves=4, seed=71)
+    n_real, seed = 11, 4242
+    P_off = np.zeros(b.n + 1, np.int64)
+    P_off[1:] = np.cumsum(b.nf)
+    stride = int(P_off[-1])
+    P = np.empty(n_real * stride, np.float32)
+    ctx = lsp.Context(0, batch_rhs=8)
+    ctx.batch_gls_noise(b.t_off, b.t, b.f0, b.df, b.nf, dy=dy, seed=seed, n_real=n_real, P_out=P, P_off=P_off,
+                        maxP=np.empty(n_real * b.n, np.float32), argmax=np.empty(n_real * b.n, np.int32))
+    ctx.close()
+    for r in (0, 5, 7, 8, 10):
+        for c in range(b.n):
+            s = slice(b.t_off[c], b.t_off[c + 1])
+            X = oracle.noise(seed, c, r, b.t_off[c + 1] - b.t_off[c]) * dy[s]
+            ref = oracle.gls_at(b.t[s], X, _grid(b.f0[c], b.df[c], b.nf[c]), dy[s])
+            base = r * stride + int(P_off[c])
+            assert_parity(P[base:base + b.nf[c]].astype(np.float64), ref, what="curve %d realization %d" % (c, r))
