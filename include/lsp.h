@@ -83,8 +83,9 @@ typedef struct lsp_options {
                                  64 .. 16,384 samples), else 1 .. 65535                 */
     int32_t timing;           /* nonzero: record per-kernel CUDA-event times            */
     int32_t mlp_fp32;         /* surrogate network: 0 = BF16 activations, 1 = FP32      */
-    int32_t batch_rhs;        /* lsp_batch with n_real > 1: realizations sharing one pass
-                                 over the samples (0 = auto, 1 = one at a time, 2|4|8)  */
+    int32_t batch_rhs;        /* lsp_batch and lsp_batch_gls_noise with n_real > 1:
+                                 realizations sharing one pass over the samples
+                                 (0 = auto, 1 = one at a time, 2|4|8)                  */
     int32_t reserved[5];      /* must be zero                                          */
 } lsp_options;
 
