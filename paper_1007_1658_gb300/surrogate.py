@@ -6,7 +6,7 @@ rate schedule, Adam, validation loss, choice of the kept weights) all run in
 liblsp.so (lsp_batch, lsp_fap_features, lsp_fap_train, lsp_fap_predict); this
 module draws sampling patterns (synth.noise_batch) and hands arrays to the C
 ABI.  The evaluation compares the library's quantiles with the empirical
-quantiles of brute-force Monte Carlo, the judge of the surrogate.
+quantiles of brute-force Monte Carlo, the yardstick the surrogate is measured against.
 
   python -m paper_1007_1658_gb300.surrogate [--quick] [--out model.lspfap] [--evaluate-only]
 
