@@ -5,7 +5,9 @@ elsewhere); every (curve, realization) periodogram is compared with the FP64
 oracle's floating-mean periodogram of that X at the parity tolerance
 (|dP| <= 1e-4 max P), with and without errors.  The noise peaks at a fixed
 frequency must follow the exact Beta(1, (N-3)/2) law, realization 0 must agree
-with lsp_batch_gls on the same X, and the refusals are checked.
+with lsp_batch_gls on the same X, groups of realizations sharing a pass must
+give the one-at-a-time results bit for bit (groups of 8 are checked against
+the oracle), and the refusals are checked.
 """
 import numpy as np
 import pytest
