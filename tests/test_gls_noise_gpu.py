@@ -44,11 +44,13 @@ def _grid(f0, df, nf):
     return f0 + np.arange(int(nf), dtype=np.float64) * df
 
 
-@pytest.mark.parametrize("weighted", [True, False])
-def test_every_realization_matches_the_oracle(lsp, weighted):
+@pytest.mark.parametrize("weighted,n_real", [(True, 5), (False, 5), (True, 1)])
+def test_every_realization_matches_the_oracle(lsp, weighted, n_real):
+    """Five realizations run as a group of 4 and a group of 1; a single one
+    runs the one-at-a-time kernel with its default strips of 16."""
     b, dy = _batch()
     d = dy if weighted else None
-    n_real, seed = 5, 20260
+    seed = 20260
     P_off = np.zeros(b.n + 1, np.int64)
     P_off[1:] = np.cumsum(b.nf + 3)  # 3 slots of slack after each curve
     stride = int(P_off[-1])
